@@ -1,0 +1,457 @@
+#!/usr/bin/env python
+"""Benchmark of the mass-consistent wind solve on the 3000 x 3000 x 15 cell
+terrain-following domain (about 1.44e8 nodes, 1.35e8 free unknowns).
+
+One step = the whole hot path on one synthetic problem: stiffness assembly
+(2x2x2 Gauss) + Galerkin hierarchy + coarsest inverse, then a cold solve
+(load vector + V-cycles to a 1e-8 relative residual) + recovery of u, then
+a warm-started solve for the next time step's wind (u0 perturbed by 2 %) +
+recovery.  value = free unknowns x V-cycles / second over the timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun: every rank solves its own replica of the domain
+(the single-domain solve does not shard here), value sums the ranks' work
+over the slowest rank's time.  --impl reference times the CPU oracle on a
+bounded window of the same domain (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("V-cycle unknowns/s and time-to-1e-8 residual at 3000×3000×15; "
+          "HBM GB/s % of peak")
+UNIT = "unknown-V-cycles/s"
+CELLS = (3000, 3000, 15)
+RTOL = 1e-8
+SAMPLE_W = 160       # CPU baseline / reference window (cells per side)
+SAMPLE_I0, SAMPLE_J0 = 1420, 1420
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mcwind", choices=["mcwind", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--cells", type=int, nargs=3, default=list(CELLS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f64-compare", action="store_true")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle on a bounded window of the same domain
+
+def oracle_step(c, cn):
+    """The oracle's own pipeline on case c: assembly + hierarchy, cold
+    V-cycle solve to 1e-8 + recovery, warm solve for wind cn + recovery.
+    Returns the V-cycles run."""
+    import oracle
+    H = oracle.Hierarchy(c)
+    f = oracle.assemble_f(c)
+    lam, h1 = H.solve(f, rtol=RTOL)
+    oracle.recover(c, lam)
+    f2 = oracle.assemble_f(c, u0=cn)
+    lam2, h2 = H.solve(f2, x0=lam, rtol=RTOL)
+    oracle.recover(c, lam2, u0=cn)
+    return (len(h1) - 1) + (len(h2) - 1)
+
+
+def sample_case(w=SAMPLE_W):
+    import synth
+    c = synth.full_domain_window(SAMPLE_I0, SAMPLE_J0, w, w)
+    cn = synth.perturb_wind(c.u0, 0)
+    return c, cn
+
+
+def run_cpu_sample(steps=1, warmup=0):
+    """Time the oracle on the window; returns a dict in the bench's unit."""
+    c, cn = sample_case()
+    for _ in range(warmup):
+        oracle_step(c, cn)
+    t0 = time.perf_counter()
+    cycles = 0
+    for _ in range(steps):
+        cycles += oracle_step(c, cn)
+    dt = time.perf_counter() - t0
+    return {"value": c.n_free * cycles / dt, "unit": UNIT, "seconds": dt, "cycles": cycles,
+            "steps": steps, "n_free": c.n_free}
+
+
+def cpu_baseline_subprocess():
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "1"],
+                         env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        return {"error": out.stderr[-400:]}
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (plain C + scipy, one thread) on cells [{SAMPLE_I0},{SAMPLE_I0 + SAMPLE_W})^2 x 15 "
+                       f"of the same domain ({r['n_free']} free unknowns): assembly + hierarchy, "
+                       f"cold + warm V-cycle solves to 1e-8, recovery; {r['cycles']} V-cycles in "
+                       f"{r['seconds']:.1f} s"),
+            "seconds": r["seconds"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    r = run_cpu_sample(steps=max(1, args.steps), warmup=max(0, args.warmup))
+    c_free = r["n_free"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * r["seconds"] / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"CPU oracle on a {SAMPLE_W}x{SAMPLE_W}x15-cell window of the "
+                               "3000x3000x15 terrain-following domain (bounded sample)",
+                   "cells": [SAMPLE_W, SAMPLE_W, 15], "n_free": c_free, "rtol": RTOL},
+        "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{SAMPLE_W}x{SAMPLE_W}x15 window, {r['cycles']} V-cycles"},
+        "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    def __init__(self, torch, dev):
+        self.proc = None
+        self.path = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+            sel = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+        except Exception:
+            sel = str(dev)
+        fields = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", sel, f"--query-gpu={fields}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+
+KINDS = ["assemble", "rap", "setup", "rhs", "outer_residual", "smooth_fine", "smooth_coarse",
+         "residual_fine", "residual_coarse", "restrict", "prolong", "coarse_solve", "update",
+         "recover", "other"]
+
+
+def read_profile(m, plan):
+    import ctypes
+    ms = (ctypes.c_double * len(KINDS))()
+    n = (ctypes.c_longlong * len(KINDS))()
+    m.lib().mcwind_profile_read(plan.handle, ms, n, len(KINDS), m._stream(None))
+    return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(run_cpu_sample(steps=1)), flush=True)
+        return 0
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_2101_08453_gb300 as m
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    m.build.build()
+    nx, ny, nz = args.cells
+    prec = m.PREC_MIXED if args.precision == "mixed" else m.PREC_F64
+    t_gen = time.perf_counter()
+    case = synth.full_domain(nx, ny, nz, seed=0)
+    u0n_np = synth.perturb_wind(case.u0, 0)
+    t_gen = time.perf_counter() - t_gen
+    n_free = case.n_free
+
+    X, Y, Z, U0, U0N = (torch.from_numpy(a).to(dev) for a in (case.X, case.Y, case.Z, case.u0, u0n_np))
+    plan = m.Plan.for_case(case, precision=prec)
+    lam = torch.zeros(plan.node_shape, dtype=torch.float64, device=dev)
+    u_c = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)
+    u_w = torch.empty_like(u_c)
+    stream = torch.cuda.current_stream()
+
+    def step(inputs=None, outputs=None, ev=None):
+        if inputs is not None:
+            for dst, src in zip((X, Y, Z, U0, U0N), inputs):
+                dst.copy_(src, non_blocking=True)
+        if ev: ev[0].record()
+        plan.assemble(X, Y, Z)
+        if ev: ev[1].record()
+        _, s1 = m.mcwind_solve(plan.handle, U0, lam, RTOL, 100, 0)
+        if ev: ev[2].record()
+        m.mcwind_recover(plan.handle, U0, lam, u_c)
+        _, s2 = m.mcwind_solve(plan.handle, U0N, lam, RTOL, 100, m.WARM)
+        if ev: ev[3].record()
+        m.mcwind_recover(plan.handle, U0N, lam, u_w)
+        if ev: ev[4].record()
+        if outputs is not None:
+            outputs[0].copy_(u_c, non_blocking=True)
+            outputs[1].copy_(u_w, non_blocking=True)
+        if s1.status != 0 or s2.status != 0:
+            raise RuntimeError(f"solve did not converge: {s1.status} {s2.status}")
+        return s1, s2
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    # ---- timed region: K steps, inputs resident in HBM -------------------
+    clocks = ClockSampler(torch, dev)
+    m.lib().mcwind_profile(plan.handle, 1, m._stream(None))
+    l0 = m.lib().mcwind_launch_count()
+    phase_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    w0 = time.perf_counter()
+    e0.record()
+    cycles = []
+    for s in range(args.steps):
+        s1, s2 = step(ev=phase_ev[s])
+        cycles.append((s1.cycles, s2.cycles, s1.rel_res, s2.rel_res, s1.rate, s2.rate))
+    e1.record()
+    barrier()
+    wall = time.perf_counter() - w0
+    launches = m.lib().mcwind_launch_count() - l0
+    prof = read_profile(m, plan)
+    m.lib().mcwind_profile(plan.handle, 0, m._stream(None))
+    clk = clocks.stop()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    work = n_free * sum(c[0] + c[1] for c in cycles)
+    phases = np.array([[phase_ev[s][q].elapsed_time(phase_ev[s][q + 1]) for q in range(4)]
+                       for s in range(args.steps)])
+    if dist is not None:
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wsum = torch.tensor([float(work)], device=dev, dtype=torch.float64)
+        dist.all_reduce(wsum, op=dist.ReduceOp.SUM)
+        t_dev, work_all = float(t), float(wsum)
+    else:
+        work_all = float(work)
+    value = work_all / t_dev
+
+    # ---- end to end through the public API with host buffers ------------
+    e2e = None
+    if not args.no_e2e:
+        pin = [torch.from_numpy(a).pin_memory() for a in (case.X, case.Y, case.Z, case.u0, u0n_np)]
+        outs = [torch.empty(u_c.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+        step(inputs=pin, outputs=outs)
+        torch.cuda.synchronize()
+        ke = max(1, min(3, args.steps))
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        ework = 0
+        for _ in range(ke):
+            s1, s2 = step(inputs=pin, outputs=outs)
+            ework += n_free * (s1.cycles + s2.cycles)
+        a1.record()
+        barrier()
+        te = a0.elapsed_time(a1) / 1e3
+        if dist is not None:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t)
+            ework *= world
+        h2d = sum(p.numel() * 8 for p in pin)
+        d2h = sum(o.numel() * 8 for o in outs)
+        e2e = {"value": ework / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * te / ke}
+        del pin, outs
+
+    # ---- time to 1e-8: mixed vs plain float64 (outside the timed region) --
+    def time_solve(p, u0, warm):
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        _, st = m.mcwind_solve(p.handle, u0, lam, RTOL, 100, m.WARM if warm else 0)
+        b1.record()
+        torch.cuda.synchronize()
+        return b0.elapsed_time(b1) / 1e3, st
+
+    lam.zero_()
+    t_cold, st_cold = time_solve(plan, U0, False)
+    t_warm, st_warm = time_solve(plan, U0N, True)
+    tt = {args.precision: {"cold_s": t_cold, "cold_cycles": st_cold.cycles,
+                           "warm_s": t_warm, "warm_cycles": st_warm.cycles,
+                           "cold_rate": st_cold.rate}}
+    prof_main = prof
+    if not args.no_f64_compare and prec == m.PREC_MIXED:
+        del plan
+        torch.cuda.empty_cache()
+        p64 = m.Plan.for_case(case, precision=m.PREC_F64)
+        p64.assemble(X, Y, Z)
+        lam.zero_()
+        time_solve(p64, U0, False)
+        lam.zero_()
+        t64c, s64c = time_solve(p64, U0, False)
+        t64w, s64w = time_solve(p64, U0N, True)
+        tt["f64"] = {"cold_s": t64c, "cold_cycles": s64c.cycles, "warm_s": t64w,
+                     "warm_cycles": s64w.cycles, "cold_rate": s64c.rate}
+        del p64
+
+    # ---- roofline of the dominant kernel class ---------------------------
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak_tflops = 1.162   # measured FP64 FMA throughput of this GB300 (2 x 5.81e11 FMA/s)
+    g0 = m.lib()
+    dims = plan_dims = (nx + 1, ny + 1, nz + 1)
+    n_nodes = plan_dims[0] * plan_dims[1] * plan_dims[2]
+    n_elem = nx * ny * nz
+    csize = 4 if prec == m.PREC_MIXED else 8
+    # algorithmic units of one launch of each class
+    algo = {
+        # bytes: 27 coefficients + f + x read + x write per free node of a column group
+        "smooth_fine": ("hbm", (27 * csize + 3 * csize) * n_free / 4.0),
+        "residual_fine": ("hbm", (27 * csize + 3 * csize) * n_free),
+        "outer_residual": ("hbm", (27 * 8 + 3 * 8 + (8 if prec == m.PREC_MIXED else 0)) * n_free),
+        # FP64 flops of one element-class launch: 8 Gauss points x (Jacobian 72, adjugate and
+        # det 21, metric 24, 8 x 9 + 36 x 3 for the element matrix) x 2 flop per FMA
+        "assemble": ("alu", 2.0 * 8 * (72 + 21 + 24 + 72 + 108) * n_elem / 8.0),
+        "rhs": ("alu", 2.0 * 8 * (72 + 21 + 24 + 9 + 24) * n_elem / 8.0),
+    }
+    dom = max((k for k in prof_main if prof_main[k][1] > 0), key=lambda k: prof_main[k][0])
+    roof_kernels = {}
+    for k, (bound, units) in algo.items():
+        ms, n = prof_main[k]
+        if n == 0:
+            continue
+        per = ms / n / 1e3
+        if bound == "hbm":
+            ach = units / per / 1e9
+            roof_kernels[k] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                               "frac": ach / hbm_peak, "ms_per_launch": per * 1e3, "launches": n}
+        else:
+            ach = units / per / 1e12
+            roof_kernels[k] = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops,
+                               "unit": "TFLOP/s", "frac": ach / fp64_peak_tflops,
+                               "ms_per_launch": per * 1e3, "launches": n}
+    dom_roof = dict(roof_kernels.get(dom, {"bound": None}))
+    dom_roof["kernel"] = dom
+    dom_roof["traffic"] = None
+    dom_roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy)" if dom_roof.get("bound") == "hbm"
+                               else "measured FP64 FMA rate of this GB300 (1.162 TFLOP/s)")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_subprocess()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == m.PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": f"{nx}x{ny}x{nz}-cell terrain-following domain (400 hills + ridge, "
+                               f"u0 from a 100x100 coarse wind): assemble + hierarchy, cold solve + "
+                               f"recover, 2%-perturbed warm solve + recover, to rtol {RTOL}",
+                   "cells": [nx, ny, nz], "n_free": n_free, "precision": args.precision,
+                   "rtol": RTOL, "levels": plan_levels if False else None,
+                   "l2": "inputs larger than L2 (X, Y, Z, u0, u0' = %.1f GB resident)" % (
+                       9 * n_nodes * 8 / 1e9),
+                   "replicas": world},
+        "gpu_launches": int(launches),
+        "cycles_per_step": {"cold": cycles[-1][0], "warm": cycles[-1][1]},
+        "rel_res": {"cold": cycles[-1][2], "warm": cycles[-1][3]},
+        "rate": {"cold": cycles[-1][4], "warm": cycles[-1][5]},
+        "phases_ms": {"setup": float(phases[:, 0].mean()), "cold_solve": float(phases[:, 1].mean()),
+                      "recover_warm_solve": float(phases[:, 2].mean()),
+                      "recover": float(phases[:, 3].mean())},
+        "time_to_1e-8": tt,
+        "vcycle_rate": {k: n_free * v["cold_cycles"] / v["cold_s"] for k, v in tt.items()},
+        "wall_s": wall,
+        "roofline": dom_roof,
+        "roofline_kernels": roof_kernels,
+        "profile_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof_main.items() if v[1]},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "input_gen_s": t_gen,
+    }
+    line["config"].pop("levels")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

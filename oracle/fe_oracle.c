@@ -237,52 +237,60 @@ int oracle_stencil_row(int nx, int ny, int nz, const double* X, const double* Y,
 }
 
 /* y = K x with the full matrix, element by element (no matrix stored).
- * Elements of even layers are done before odd layers; within a parity
- * class the layers are independent, so they may run in parallel. */
+ * Elements are visited in 4 classes by the parities of (j, k); two element
+ * rows (j, k) of one class share no node, so the rows of a class may run in
+ * parallel. */
 int oracle_apply_K(int nx, int ny, int nz, const double* X, const double* Y, const double* Z,
                    const double* a, const double* x, double* y) {
   int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   memset(y, 0, N * sizeof(double));
   int bad = 0;
-  for (int parity = 0; parity < 2; ++parity) {
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
-    for (int k = parity; k < nz; k += 2)
-      for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-          double xe[8][3], Ke[64];
-          gather_xe(nx, ny, X, Y, Z, i, j, k, xe);
-          if (oracle_element_stiffness(&xe[0][0], a, Ke)) { bad = 1; continue; }
-          int64_t id[8];
-          for (int n = 0; n < 8; ++n)
-            id[n] = nid(nx, ny, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
-          for (int m = 0; m < 8; ++m) {
-            double s = 0.0;
-            for (int n = 0; n < 8; ++n) s += Ke[m * 8 + n] * x[id[n]];
-            y[id[m]] += s;
-          }
+  for (int cls = 0; cls < 4; ++cls) {
+    int pj = cls & 1, pk = cls >> 1;
+    int nj = (ny - pj + 1) / 2, nk = (nz - pk + 1) / 2;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+    for (int64_t q = 0; q < (int64_t)nj * nk; ++q) {
+      int j = pj + 2 * (int)(q % nj), k = pk + 2 * (int)(q / nj);
+      for (int i = 0; i < nx; ++i) {
+        double xe[8][3], Ke[64];
+        gather_xe(nx, ny, X, Y, Z, i, j, k, xe);
+        if (oracle_element_stiffness(&xe[0][0], a, Ke)) { bad = 1; continue; }
+        int64_t id[8];
+        for (int n = 0; n < 8; ++n)
+          id[n] = nid(nx, ny, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+        for (int m = 0; m < 8; ++m) {
+          double sum = 0.0;
+          for (int n = 0; n < 8; ++n) sum += Ke[m * 8 + n] * x[id[n]];
+          y[id[m]] += sum;
         }
+      }
+    }
   }
   return bad ? ORACLE_EGEOM : 0;
 }
 
-/* Same as oracle_assemble_rhs, parallel over layers of one parity at a time. */
+/* Same as oracle_assemble_rhs, the element rows in 4 parity classes of
+ * (j, k) as in oracle_apply_K, rows of a class in parallel. */
 int oracle_assemble_rhs_par(int nx, int ny, int nz, const double* X, const double* Y,
                             const double* Z, const double* u0, int quad, double* f) {
   int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   memset(f, 0, N * sizeof(double));
   int bad = 0;
-  for (int parity = 0; parity < 2; ++parity) {
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
-    for (int k = parity; k < nz; k += 2)
-      for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-          double xe[8][3], ue[8][3], fe[8];
-          gather_xe(nx, ny, X, Y, Z, i, j, k, xe);
-          gather_u(nx, ny, nz, u0, i, j, k, ue);
-          if (oracle_element_rhs(&xe[0][0], &ue[0][0], quad, fe)) { bad = 1; continue; }
-          for (int m = 0; m < 8; ++m)
-            f[nid(nx, ny, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] += fe[m];
-        }
+  for (int cls = 0; cls < 4; ++cls) {
+    int pj = cls & 1, pk = cls >> 1;
+    int nj = (ny - pj + 1) / 2, nk = (nz - pk + 1) / 2;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+    for (int64_t q = 0; q < (int64_t)nj * nk; ++q) {
+      int j = pj + 2 * (int)(q % nj), k = pk + 2 * (int)(q / nj);
+      for (int i = 0; i < nx; ++i) {
+        double xe[8][3], ue[8][3], fe[8];
+        gather_xe(nx, ny, X, Y, Z, i, j, k, xe);
+        gather_u(nx, ny, nz, u0, i, j, k, ue);
+        if (oracle_element_rhs(&xe[0][0], &ue[0][0], quad, fe)) { bad = 1; continue; }
+        for (int m = 0; m < 8; ++m)
+          f[nid(nx, ny, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] += fe[m];
+      }
+    }
   }
   return bad ? ORACLE_EGEOM : 0;
 }

@@ -1,0 +1,575 @@
+// C entry points and the solve driver.
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+
+using namespace mcw;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+#define CK(expr)                                      \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) {                          \
+      g_last_cuda = (int)e_;                          \
+      return MCWIND_ECUDA;                            \
+    }                                                 \
+  } while (0)
+
+#define CKR(expr)                                     \
+  do {                                                \
+    int r_ = (expr);                                  \
+    if (r_ != MCWIND_OK) return r_;                   \
+  } while (0)
+
+long long launches_now() { return mcwind_launch_count(); }
+
+// Records a CUDA event pair around a kernel class while profiling is on.
+struct ProfScope {
+  mcwind_plan p;
+  int kind;
+  cudaStream_t st;
+  long long n0 = 0;
+  bool on = false;
+  ProfScope(mcwind_plan p_, int kind_, cudaStream_t st_) : p(p_), kind(kind_), st(st_) {
+    if (!p->prof) return;
+    if (p->ev_used + 2 > p->ev_pool.size()) {
+      for (int q = 0; q < 256; ++q) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        p->ev_pool.push_back(e);
+      }
+    }
+    if (cudaEventRecord(p->ev_pool[p->ev_used], st) != cudaSuccess) return;
+    on = true;
+    n0 = launches_now();
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(p->ev_pool[p->ev_used + 1], st);
+    p->ev_used += 2;
+    p->prof_marks.push_back({kind, (int)(launches_now() - n0)});
+  }
+};
+
+// fold recorded event pairs into the per-class totals (stream must be idle)
+void prof_fold(mcwind_plan p) {
+  for (size_t q = 0; q < p->prof_marks.size(); ++q) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p->ev_pool[2 * q], p->ev_pool[2 * q + 1]) == cudaSuccess)
+      p->prof_ms[p->prof_marks[q].first] += ms;
+    p->prof_n[p->prof_marks[q].first] += p->prof_marks[q].second;
+  }
+  p->prof_marks.clear();
+  p->ev_used = 0;
+}
+
+#define PROF_CAT2(a, b) a##b
+#define PROF_CAT(a, b) PROF_CAT2(a, b)
+#define PROF(kind) ProfScope PROF_CAT(prof_scope_, __LINE__)(p, (kind), st)
+
+template <typename P>
+P* at(mcwind_plan p, P* offset) {
+  return (P*)(p->ws + (size_t)offset);
+}
+
+double* scal(mcwind_plan p) { return (double*)(p->ws + p->off_scalars); }
+int* flagp(mcwind_plan p) { return (int*)(p->ws + p->off_scalars + 128); }
+double* partials(mcwind_plan p) { return (double*)(p->ws + p->off_partials); }
+int* cfree(mcwind_plan p) { return (int*)(p->ws + p->off_cfree); }
+
+struct Ptr64 {
+  double *C, *x, *f, *r;
+};
+struct Ptr32 {
+  float *C, *x, *f, *r;
+};
+
+Ptr64 lv64(mcwind_plan p, int l) {
+  Level& L = p->lv[l];
+  return {at(p, L.C64), at(p, L.x64), at(p, L.f64), at(p, L.r64)};
+}
+Ptr32 lv32(mcwind_plan p, int l) {
+  Level& L = p->lv[l];
+  return {at(p, L.C32), at(p, L.x32), at(p, L.f32), at(p, L.r32)};
+}
+
+template <typename T>
+struct Sel;
+template <>
+struct Sel<double> {
+  static Ptr64 get(mcwind_plan p, int l) { return lv64(p, l); }
+};
+template <>
+struct Sel<float> {
+  static Ptr32 get(mcwind_plan p, int l) { return lv32(p, l); }
+};
+
+double* dense_inv(mcwind_plan p) {
+  // result of the Gauss-Jordan ping-pong: n even -> first buffer, odd -> second
+  double* A = (double*)(p->ws + p->off_dense);
+  return (p->n_coarse % 2 == 0) ? A : A + (size_t)p->n_coarse * p->n_coarse;
+}
+
+template <typename T>
+int smooth(mcwind_plan p, int l, int sweeps, int direction, cudaStream_t st) {
+  auto P = Sel<T>::get(p, l);
+  const Grid& g = p->lv[l].g;
+  PROF(l == 0 ? MCWIND_K_SMOOTH_FINE : MCWIND_K_SMOOTH_COARSE);
+  for (int s = 0; s < sweeps; ++s)
+    for (int q = 0; q < 4; ++q) {
+      const int grp = direction == MCWIND_FORWARD ? q : 3 - q;
+      CK(launch_gs_group<T>(g, P.C, P.f, P.x, grp, direction == MCWIND_FORWARD ? 1 : 0, st));
+    }
+  return MCWIND_OK;
+}
+
+template <typename T>
+int vcycle(mcwind_plan p, int l, cudaStream_t st) {
+  const int last = (int)p->lv.size() - 1;
+  auto P = Sel<T>::get(p, l);
+  Level& L = p->lv[l];
+  if (l == last) {
+    PROF(MCWIND_K_COARSE_SOLVE);
+    CK(launch_dense_solve<T>(dense_inv(p), p->n_coarse, cfree(p), P.f, P.x, st));
+    return MCWIND_OK;
+  }
+  if (l > 0) CK(cudaMemsetAsync(P.x, 0, sizeof(T) * (size_t)L.g.total, st));
+  CKR(smooth<T>(p, l, p->opt.nu_pre, MCWIND_FORWARD, st));
+  {
+    PROF(l == 0 ? MCWIND_K_RESIDUAL_FINE : MCWIND_K_RESIDUAL_COARSE);
+    CK(launch_residual<T>(L.g, P.C, P.f, P.x, P.r, nullptr, nullptr, st));
+  }
+  auto Q = Sel<T>::get(p, l + 1);
+  {
+    PROF(MCWIND_K_RESTRICT);
+    CK(launch_restrict<T>(L.g, p->lv[l + 1].g, L.tr, P.r, Q.f, st));
+  }
+  CKR(vcycle<T>(p, l + 1, st));
+  {
+    PROF(MCWIND_K_PROLONG);
+    CK(launch_prolong_add<T>(L.g, p->lv[l + 1].g, L.tr, Q.x, P.x, st));
+  }
+  CKR(smooth<T>(p, l, p->opt.nu_post, p->opt.post_reverse ? MCWIND_BACKWARD : MCWIND_FORWARD, st));
+  return MCWIND_OK;
+}
+
+int check_level(mcwind_plan p, int level, int precision) {
+  if (!p) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  if (level < 0 || level >= (int)p->lv.size()) return MCWIND_EINVAL;
+  if (precision != MCWIND_PREC_F64 && precision != MCWIND_PREC_MIXED) return MCWIND_EINVAL;
+  if (precision == MCWIND_PREC_MIXED && p->opt.precision != MCWIND_PREC_MIXED) return MCWIND_EINVAL;
+  return MCWIND_OK;
+}
+
+// ||v_F||^2 of a float64 split-layout vector into scal[slot]
+int norm2(mcwind_plan p, const Grid& g, const double* v, int slot, cudaStream_t st) {
+  PROF(MCWIND_K_OTHER);
+  int nb = 0;
+  CK(launch_norm2_partials(g, v, partials(p), &nb, st));
+  CK(launch_reduce_final(partials(p), nb, scal(p) + slot, st));
+  return MCWIND_OK;
+}
+
+// residual of the outer float64 iteration on level 0 and its squared norm in scal[1];
+// in mixed mode also the float32 right side and a zero start of the correction.
+int outer_residual(mcwind_plan p, cudaStream_t st) {
+  Ptr64 A = lv64(p, 0);
+  const Grid& g = p->lv[0].g;
+  int nb = 0;
+  PROF(MCWIND_K_OUTER_RESIDUAL);
+  if (p->opt.precision == MCWIND_PREC_F64) {
+    CK(launch_residual<double>(g, A.C, A.f, A.x, A.r, partials(p), &nb, st));
+  } else {
+    Ptr32 B = lv32(p, 0);
+    CK(launch_residual_mixed(g, A.C, A.f, A.x, B.f, B.x, partials(p), &nb, st));
+  }
+  CK(launch_reduce_final(partials(p), nb, scal(p) + 1, st));
+  return MCWIND_OK;
+}
+
+int one_cycle(mcwind_plan p, cudaStream_t st) {
+  if (p->opt.precision == MCWIND_PREC_F64) {
+    CKR(vcycle<double>(p, 0, st));
+  } else {
+    CKR(vcycle<float>(p, 0, st));
+    PROF(MCWIND_K_UPDATE);
+    CK(launch_update_mixed(p->lv[0].g, lv64(p, 0).x, lv32(p, 0).x, st));
+  }
+  return outer_residual(p, st);
+}
+
+// copy device scalars [first, first + n) to host (synchronizes the stream)
+int read_scalars(mcwind_plan p, double* host, int first, int n, cudaStream_t st) {
+  CK(cudaMemcpyAsync(host, scal(p) + first, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (p->prof) prof_fold(p);
+  return MCWIND_OK;
+}
+
+}  // namespace
+
+extern "C" int mcwind_last_cuda_error(void) { return g_last_cuda; }
+
+extern "C" const char* mcwind_strerror(int code) {
+  switch (code) {
+    case MCWIND_OK: return "ok";
+    case MCWIND_EINVAL: return "invalid argument";
+    case MCWIND_EGEOM: return "inverted or degenerate element (detJ <= 0)";
+    case MCWIND_ENONFINITE: return "non-finite input wind";
+    case MCWIND_ENOTCONV: return "not converged within max_cycles";
+    case MCWIND_ECUDA: return "CUDA error";
+    case MCWIND_ESTATE: return "plan not assembled";
+    case MCWIND_ETIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+extern "C" void mcwind_plan_destroy(mcwind_plan p) {
+  if (!p) return;
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  delete p;
+}
+
+extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, const double* Y,
+                               const double* Z, void* stream) {
+  if (!p || !workspace || !X || !Y || !Z) return MCWIND_EINVAL;
+  if (((uintptr_t)workspace) % 256 != 0) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  p->ws = (char*)workspace;
+  p->X = X; p->Y = Y; p->Z = Z;
+  p->assembled = false;
+  // zero level-0 planes (assembly accumulates into them) and every vector
+  for (size_t l = 0; l < p->lv.size(); ++l) {
+    Level& L = p->lv[l];
+    const size_t t = (size_t)L.g.total;
+    if (l == 0) CK(cudaMemsetAsync(at(p, L.C64), 0, kPlanes * t * 8, st));
+    Ptr64 A = lv64(p, (int)l);
+    CK(cudaMemsetAsync(A.x, 0, 3 * ((t * 8 + 255) / 256 * 256), st));
+    if (p->opt.precision == MCWIND_PREC_MIXED) {
+      Ptr32 B = lv32(p, (int)l);
+      CK(cudaMemsetAsync(B.x, 0, 3 * ((t * 4 + 255) / 256 * 256), st));
+    }
+  }
+  CK(cudaMemsetAsync(p->ws + p->off_scalars, 0, 256, st));
+  Level& L0 = p->lv[0];
+  {
+    PROF(MCWIND_K_ASSEMBLE);
+    CK(launch_assemble_stencil(L0.g, p->nx, p->ny, p->nz, X, Y, Z, p->a, at(p, L0.C64), flagp(p), st));
+  }
+  {
+    PROF(MCWIND_K_SETUP);
+    CK(launch_stencil_finalize(L0.g, at(p, L0.C64), flagp(p), st));
+  }
+  double* tmpA = (double*)(p->ws + p->off_tmp);
+  double* tmpB = (double*)(p->ws + p->off_tmp + p->tmp_bytes);
+  for (size_t l = 0; l + 1 < p->lv.size(); ++l) {
+    Level& F = p->lv[l];
+    Level& Cl = p->lv[l + 1];
+    struct Stage { int dim; Grid gout; };
+    std::vector<Stage> stages;
+    int nxg = F.g.Nx, nyg = F.g.Ny;
+    if (F.hx) { nxg = Cl.g.Nx; stages.push_back({0, make_grid(nxg, nyg, F.g.Nz)}); }
+    if (F.hy) { nyg = Cl.g.Ny; stages.push_back({1, make_grid(nxg, nyg, F.g.Nz)}); }
+    if (Cl.g.Nz != F.g.Nz) stages.push_back({2, Cl.g});
+    const double* src = at(p, F.C64);
+    Grid gin = F.g;
+    for (size_t s = 0; s < stages.size(); ++s) {
+      double* dst = (s + 1 == stages.size()) ? at(p, Cl.C64) : (s == 0 ? tmpA : tmpB);
+      PROF(MCWIND_K_RAP);
+      CK(launch_rap_stage(stages[s].dim, gin, stages[s].gout, F.tr, src, dst, st));
+      src = dst;
+      gin = stages[s].gout;
+    }
+    PROF(MCWIND_K_SETUP);
+    CK(launch_stencil_finalize(Cl.g, at(p, Cl.C64), flagp(p), st));
+  }
+  PROF(MCWIND_K_SETUP);
+  if (p->opt.precision == MCWIND_PREC_MIXED)
+    for (size_t l = 0; l < p->lv.size(); ++l)
+      CK(launch_stencil_to_f32(p->lv[l].g, at(p, p->lv[l].C64), at(p, p->lv[l].C32), st));
+  // coarsest direct solver
+  Level& Lc = p->lv.back();
+  double* A = (double*)(p->ws + p->off_dense);
+  double* B = A + (size_t)p->n_coarse * p->n_coarse;
+  CK(launch_coarse_index(Lc.g, cfree(p), st));
+  CK(launch_dense_gather(Lc.g, at(p, Lc.C64), cfree(p), p->n_coarse, A, st));
+  double* res = nullptr;
+  CK(launch_dense_invert(A, B, p->n_coarse, &res, st));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, flagp(p), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (p->prof) prof_fold(p);
+  if (flag) return MCWIND_EGEOM;
+  p->assembled = true;
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_rhs(mcwind_plan p, const double* u0, double* f, void* stream) {
+  if (!p || !u0 || !f) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& L0 = p->lv[0];
+  Ptr64 A = lv64(p, 0);
+  CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, st));
+  CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, p->opt.rhs_quad, A.f, st));
+  CK(launch_split_to_std<double>(L0.g, A.f, f, st));
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_solve(mcwind_plan p, const double* u0, double* lambda, double rtol,
+                            int max_cycles, unsigned flags, mcwind_stats* stats, void* stream) {
+  if (!p || !u0 || !lambda) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  if (max_cycles < 0 || max_cycles >= MCWIND_HIST || !(rtol >= 0.0)) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& L0 = p->lv[0];
+  Ptr64 A = lv64(p, 0);
+  // load vector f (Eq. 5 right side) and its norm
+  {
+    PROF(MCWIND_K_RHS);
+    CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, st));
+    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, p->opt.rhs_quad, A.f, st));
+  }
+  CKR(norm2(p, L0.g, A.f, 0, st));
+  {
+    PROF(MCWIND_K_OTHER);
+    if (flags & MCWIND_WARM)
+      CK(launch_std_to_split<double>(L0.g, lambda, A.x, true, st));
+    else
+      CK(cudaMemsetAsync(A.x, 0, sizeof(double) * (size_t)L0.g.total, st));
+  }
+  CKR(outer_residual(p, st));
+  double h[2];
+  CKR(read_scalars(p, h, 0, 2, st));
+  const double nf = std::sqrt(h[0]);
+  mcwind_stats S;
+  std::memset(&S, 0, sizeof(S));
+  S.norm_f = nf;
+  if (!std::isfinite(nf) || !std::isfinite(h[1])) {
+    if (stats) { S.status = MCWIND_ENONFINITE; *stats = S; }
+    return MCWIND_ENONFINITE;
+  }
+  int status = MCWIND_OK;
+  if (nf == 0.0) {
+    CK(cudaMemsetAsync(A.x, 0, sizeof(double) * (size_t)L0.g.total, st));
+    S.res_hist[0] = 0.0;
+  } else {
+    S.res_hist[0] = std::sqrt(h[1]) / nf;
+    int c = 0;
+    while (S.res_hist[c] > rtol && c < max_cycles) {
+      CKR(one_cycle(p, st));
+      CKR(read_scalars(p, h + 1, 1, 1, st));
+      ++c;
+      S.res_hist[c] = std::sqrt(h[1]) / nf;
+      if (!std::isfinite(S.res_hist[c])) break;
+    }
+    S.cycles = c;
+    if (!(S.res_hist[c] <= rtol)) status = MCWIND_ENOTCONV;
+  }
+  S.rel_res = S.res_hist[S.cycles];
+  if (S.cycles >= 3 && S.res_hist[2] > 0.0)
+    S.rate = std::pow(S.res_hist[S.cycles] / S.res_hist[2], 1.0 / (S.cycles - 2));
+  else if (S.cycles >= 1 && S.res_hist[0] > 0.0)
+    S.rate = std::pow(S.res_hist[S.cycles] / S.res_hist[0], 1.0 / S.cycles);
+  S.status = status;
+  {
+    PROF(MCWIND_K_OTHER);
+    CK(launch_split_to_std<double>(L0.g, A.x, lambda, st));
+  }
+  if (stats) *stats = S;
+  return status;
+}
+
+extern "C" int mcwind_recover(mcwind_plan p, const double* u0, const double* lambda, double* u,
+                              int where, void* stream) {
+  if (!p || !u0 || !lambda || !u) return MCWIND_EINVAL;
+  if (where != MCWIND_AT_CENTERS && where != MCWIND_AT_GAUSS) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& L0 = p->lv[0];
+  double* lam = lv64(p, 0).r;  // scratch: lambda in the split layout
+  {
+    PROF(MCWIND_K_OTHER);
+    CK(launch_std_to_split<double>(L0.g, lambda, lam, true, st));
+  }
+  PROF(MCWIND_K_RECOVER);
+  CK(launch_recover(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, lam, p->a, where, u, st));
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_weak_div(mcwind_plan p, const double* ug, double* out, void* stream) {
+  if (!p || !ug || !out) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t n = (size_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1);
+  CK(cudaMemsetAsync(out, 0, n * sizeof(double), st));
+  CK(launch_weak_div(p->nx, p->ny, p->nz, p->X, p->Y, p->Z, ug, out, st));
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_level_stencil(mcwind_plan p, int level, int precision, double* out,
+                                    void* stream) {
+  CKR(check_level(p, level, precision));
+  if (!out) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Grid& g = p->lv[level].g;
+  if (precision == MCWIND_PREC_F64)
+    CK(launch_stencil_export<double>(g, lv64(p, level).C, out, st));
+  else
+    CK(launch_stencil_export<float>(g, lv32(p, level).C, out, st));
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_level_residual(mcwind_plan p, int level, int precision, const double* x,
+                                     const double* f, double* r, void* stream) {
+  CKR(check_level(p, level, precision));
+  if (!x || !f || !r) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Grid& g = p->lv[level].g;
+  if (precision == MCWIND_PREC_F64) {
+    Ptr64 P = lv64(p, level);
+    CK(launch_std_to_split<double>(g, x, P.x, true, st));
+    CK(launch_std_to_split<double>(g, f, P.f, true, st));
+    CK(launch_residual<double>(g, P.C, P.f, P.x, P.r, nullptr, nullptr, st));
+    CK(launch_split_to_std<double>(g, P.r, r, st));
+  } else {
+    Ptr32 P = lv32(p, level);
+    CK(launch_std_to_split<float>(g, x, P.x, true, st));
+    CK(launch_std_to_split<float>(g, f, P.f, true, st));
+    CK(launch_residual<float>(g, P.C, P.f, P.x, P.r, nullptr, nullptr, st));
+    CK(launch_split_to_std<float>(g, P.r, r, st));
+  }
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_level_smooth(mcwind_plan p, int level, int precision, double* x,
+                                   const double* f, int sweeps, int direction, void* stream) {
+  CKR(check_level(p, level, precision));
+  if (!x || !f || sweeps < 0) return MCWIND_EINVAL;
+  if (direction != MCWIND_FORWARD && direction != MCWIND_BACKWARD) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Grid& g = p->lv[level].g;
+  if (precision == MCWIND_PREC_F64) {
+    Ptr64 P = lv64(p, level);
+    CK(launch_std_to_split<double>(g, x, P.x, true, st));
+    CK(launch_std_to_split<double>(g, f, P.f, true, st));
+    CKR(smooth<double>(p, level, sweeps, direction, st));
+    CK(launch_split_to_std<double>(g, P.x, x, st));
+  } else {
+    Ptr32 P = lv32(p, level);
+    CK(launch_std_to_split<float>(g, x, P.x, true, st));
+    CK(launch_std_to_split<float>(g, f, P.f, true, st));
+    CKR(smooth<float>(p, level, sweeps, direction, st));
+    CK(launch_split_to_std<float>(g, P.x, x, st));
+  }
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_level_restrict(mcwind_plan p, int level, int precision, const double* r,
+                                     double* fc, void* stream) {
+  CKR(check_level(p, level, precision));
+  if (level + 1 >= (int)p->lv.size() || !r || !fc) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& F = p->lv[level];
+  const Grid& gc = p->lv[level + 1].g;
+  if (precision == MCWIND_PREC_F64) {
+    Ptr64 P = lv64(p, level), Q = lv64(p, level + 1);
+    CK(launch_std_to_split<double>(F.g, r, P.r, true, st));
+    CK(launch_restrict<double>(F.g, gc, F.tr, P.r, Q.f, st));
+    CK(launch_split_to_std<double>(gc, Q.f, fc, st));
+  } else {
+    Ptr32 P = lv32(p, level), Q = lv32(p, level + 1);
+    CK(launch_std_to_split<float>(F.g, r, P.r, true, st));
+    CK(launch_restrict<float>(F.g, gc, F.tr, P.r, Q.f, st));
+    CK(launch_split_to_std<float>(gc, Q.f, fc, st));
+  }
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_level_prolong(mcwind_plan p, int level, int precision, const double* ec,
+                                    double* x, void* stream) {
+  CKR(check_level(p, level, precision));
+  if (level + 1 >= (int)p->lv.size() || !ec || !x) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Level& F = p->lv[level];
+  const Grid& gc = p->lv[level + 1].g;
+  if (precision == MCWIND_PREC_F64) {
+    Ptr64 P = lv64(p, level), Q = lv64(p, level + 1);
+    CK(launch_std_to_split<double>(gc, ec, Q.x, true, st));
+    CK(launch_std_to_split<double>(F.g, x, P.x, true, st));
+    CK(launch_prolong_add<double>(F.g, gc, F.tr, Q.x, P.x, st));
+    CK(launch_split_to_std<double>(F.g, P.x, x, st));
+  } else {
+    Ptr32 P = lv32(p, level), Q = lv32(p, level + 1);
+    CK(launch_std_to_split<float>(gc, ec, Q.x, true, st));
+    CK(launch_std_to_split<float>(F.g, x, P.x, true, st));
+    CK(launch_prolong_add<float>(F.g, gc, F.tr, Q.x, P.x, st));
+    CK(launch_split_to_std<float>(F.g, P.x, x, st));
+  }
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_coarse_solve(mcwind_plan p, const double* f, double* x, void* stream) {
+  if (!p || !f || !x) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int last = (int)p->lv.size() - 1;
+  const Grid& g = p->lv[last].g;
+  Ptr64 P = lv64(p, last);
+  CK(launch_std_to_split<double>(g, f, P.f, true, st));
+  CK(cudaMemsetAsync(P.x, 0, sizeof(double) * (size_t)g.total, st));
+  CK(launch_dense_solve<double>(dense_inv(p), p->n_coarse, cfree(p), P.f, P.x, st));
+  CK(launch_split_to_std<double>(g, P.x, x, st));
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_vcycle(mcwind_plan p, int precision, double* x, const double* f,
+                             void* stream) {
+  CKR(check_level(p, 0, precision));
+  if (!x || !f) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Grid& g = p->lv[0].g;
+  if (precision == MCWIND_PREC_F64) {
+    Ptr64 P = lv64(p, 0);
+    CK(launch_std_to_split<double>(g, x, P.x, true, st));
+    CK(launch_std_to_split<double>(g, f, P.f, true, st));
+    CKR(vcycle<double>(p, 0, st));
+    CK(launch_split_to_std<double>(g, P.x, x, st));
+  } else {
+    Ptr32 P = lv32(p, 0);
+    CK(launch_std_to_split<float>(g, x, P.x, true, st));
+    CK(launch_std_to_split<float>(g, f, P.f, true, st));
+    CKR(vcycle<float>(p, 0, st));
+    CK(launch_split_to_std<float>(g, P.x, x, st));
+  }
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_profile(mcwind_plan p, int enable, void* stream) {
+  if (!p) return MCWIND_EINVAL;
+  if (enable) {
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    p->prof_marks.clear();
+    p->ev_used = 0;
+    for (int k = 0; k < MCWIND_K_KINDS; ++k) { p->prof_ms[k] = 0.0; p->prof_n[k] = 0; }
+  }
+  p->prof = enable != 0;
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_profile_read(mcwind_plan p, double* ms, long long* launches, int nkinds,
+                                   void* stream) {
+  if (!p || nkinds < 0 || (nkinds > 0 && (!ms || !launches))) return MCWIND_EINVAL;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  prof_fold(p);
+  for (int k = 0; k < nkinds && k < MCWIND_K_KINDS; ++k) {
+    ms[k] = p->prof_ms[k];
+    launches[k] = p->prof_n[k];
+  }
+  return MCWIND_K_KINDS;
+}

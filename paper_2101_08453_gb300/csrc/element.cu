@@ -1,0 +1,394 @@
+// Element kernels: isoparametric 8-node hexahedra (Sec. 2 of the paper).
+//
+// Local node n = a + 2b + 4c of element (i, j, k) is grid node
+// (i+a, j+b, k+c) with reference corner (2a-1, 2b-1, 2c-1).  The Jacobian
+// J[d][r] = dx_d/dxi_r of the trilinear map is evaluated from the 12 edge
+// vectors: column r at a point depends only on the other two reference
+// coordinates, through a bilinear blend of the 4 edges parallel to r.
+// With adj = det(J) J^{-1}:
+//   detJ grad N_m . A^{-1} grad N_n = dN_m^T (adj D adj^T / detJ) dN_n,
+//   detJ grad N_m . v               = dN_m^T (adj v),       D = diag(a^-2).
+// Assembly scatters element contributions in 8 launches, one per element
+// parity class (i mod 2, j mod 2, k mod 2): elements of one class share no
+// node, so there are no atomics and the sums are deterministic.
+#include "kernels.cuh"
+
+namespace mcw {
+namespace {
+
+constexpr double kGp = 0.57735026918962576451;  // 1/sqrt(3), the 2-point Gauss abscissa
+
+struct Geo {
+  double e[3][4][3];  // e[r][q][d]: edge vectors parallel to reference axis r
+};
+
+__device__ __forceinline__ int64_t sidx(int nx1, int ny1, int i, int j, int k) {
+  return ((int64_t)k * ny1 + j) * nx1 + i;
+}
+
+// Edge vectors of element (i, j, k).  For axis r the 4 parallel edges are
+// indexed q = q1 + 2 q2 by the node bits of the other two axes (in
+// increasing axis order).
+__device__ __forceinline__ void load_geo(const double* X, const double* Y, const double* Z,
+                                         int nx1, int ny1, int i, int j, int k, Geo& G) {
+  double xe[8][3];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    int64_t id = sidx(nx1, ny1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+    xe[n][0] = X[id];
+    xe[n][1] = Y[id];
+    xe[n][2] = Z[id];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int q1 = q & 1, q2 = q >> 1;
+    int nx0 = 0 + 2 * q1 + 4 * q2;   // axis 0 edge: b = q1, c = q2
+    int ny0 = q1 + 0 + 4 * q2;       // axis 1 edge: a = q1, c = q2
+    int nz0 = q1 + 2 * q2 + 0;       // axis 2 edge: a = q1, b = q2
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      G.e[0][q][d] = xe[nx0 + 1][d] - xe[nx0][d];
+      G.e[1][q][d] = xe[ny0 + 2][d] - xe[ny0][d];
+      G.e[2][q][d] = xe[nz0 + 4][d] - xe[nz0][d];
+    }
+  }
+}
+
+// Jacobian at reference point xi: J[d][r] = 1/8 sum_q e[r][q][d] (1+s1 t1)(1+s2 t2),
+// (t1, t2) = the other two coordinates of xi, s = -1/+1 by the edge's node bits.
+__device__ __forceinline__ void jacobian_at(const Geo& G, const double xi[3], double J[3][3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double t1 = (r == 0) ? xi[1] : xi[0];
+    double t2 = (r == 2) ? xi[1] : xi[2];
+    double w[4];
+    w[0] = 0.125 * (1.0 - t1) * (1.0 - t2);
+    w[1] = 0.125 * (1.0 + t1) * (1.0 - t2);
+    w[2] = 0.125 * (1.0 - t1) * (1.0 + t2);
+    w[3] = 0.125 * (1.0 + t1) * (1.0 + t2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      J[d][r] = w[0] * G.e[r][0][d] + w[1] * G.e[r][1][d] + w[2] * G.e[r][2][d] +
+                w[3] * G.e[r][3][d];
+  }
+}
+
+// adj[r][d] = det(J) * (J^{-1})[r][d]; returns det(J).
+__device__ __forceinline__ double adjugate(const double J[3][3], double adj[3][3]) {
+  adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+}
+
+// reference gradient of shape function n at xi
+__device__ __forceinline__ void dshape(int n, const double xi[3], double dN[3]) {
+  double c0 = (n & 1) ? 1.0 : -1.0, c1 = (n & 2) ? 1.0 : -1.0, c2 = (n & 4) ? 1.0 : -1.0;
+  double f0 = 1.0 + c0 * xi[0], f1 = 1.0 + c1 * xi[1], f2 = 1.0 + c2 * xi[2];
+  dN[0] = 0.125 * c0 * f1 * f2;
+  dN[1] = 0.125 * f0 * c1 * f2;
+  dN[2] = 0.125 * f0 * f1 * c2;
+}
+
+__device__ __forceinline__ double shape(int n, const double xi[3]) {
+  double c0 = (n & 1) ? 1.0 : -1.0, c1 = (n & 2) ? 1.0 : -1.0, c2 = (n & 4) ? 1.0 : -1.0;
+  return 0.125 * (1.0 + c0 * xi[0]) * (1.0 + c1 * xi[1]) * (1.0 + c2 * xi[2]);
+}
+
+__device__ __forceinline__ void gauss_xi(int g, double xi[3]) {
+  xi[0] = (g & 1) ? kGp : -kGp;
+  xi[1] = (g & 2) ? kGp : -kGp;
+  xi[2] = (g & 4) ? kGp : -kGp;
+}
+
+// Thread -> element of parity class (pi, pj, pk).
+__device__ __forceinline__ bool elem_of_thread(int nx, int ny, int nz, int cls, int& i, int& j,
+                                               int& k) {
+  i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + (cls & 1);
+  j = 2 * (int)(blockIdx.y * blockDim.y + threadIdx.y) + ((cls >> 1) & 1);
+  k = 2 * (int)blockIdx.z + ((cls >> 2) & 1);
+  return i < nx && j < ny && k < nz;
+}
+
+__global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny, int nz,
+                                                          const double* __restrict__ X,
+                                                          const double* __restrict__ Y,
+                                                          const double* __restrict__ Z,
+                                                          double d0, double d1, double d2,
+                                                          double* __restrict__ C, int* flag,
+                                                          int cls) {
+  int i, j, k;
+  if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
+  Geo G;
+  load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+  double Ke[8][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+#pragma unroll
+    for (int n = 0; n < 8; ++n) Ke[m][n] = 0.0;
+  bool bad = false;
+#pragma unroll 1
+  for (int gp = 0; gp < 8; ++gp) {
+    double xi[3], J[3][3], adj[3][3];
+    gauss_xi(gp, xi);
+    jacobian_at(G, xi, J);
+    double det = adjugate(J, adj);
+    bad |= !(det > 0.0);
+    double inv = 1.0 / det;
+    // Cm = adj D adj^T / det (symmetric)
+    double Cm[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int t = r; t < 3; ++t) {
+        double s = adj[r][0] * adj[t][0] * d0 + adj[r][1] * adj[t][1] * d1 +
+                   adj[r][2] * adj[t][2] * d2;
+        Cm[r][t] = s * inv;
+        Cm[t][r] = s * inv;
+      }
+    double dN[8][3], v[8][3];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      dshape(n, xi, dN[n]);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        v[n][r] = Cm[r][0] * dN[n][0] + Cm[r][1] * dN[n][1] + Cm[r][2] * dN[n][2];
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+#pragma unroll
+      for (int n = m; n < 8; ++n)
+        Ke[m][n] += dN[m][0] * v[n][0] + dN[m][1] * v[n][1] + dN[m][2] * v[n][2];
+  }
+  if (bad) atomicOr(flag, 1);
+  // scatter: row of local node m gets Ke[m][n] at offset (n - m)
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
+    if (!is_free(g, im, jm, km)) continue;
+    int64_t row = gidx(g, im, jm, km);
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      int in = i + (n & 1), jn = j + ((n >> 1) & 1), kn = k + ((n >> 2) & 1);
+      if (!is_free(g, in, jn, kn)) continue;
+      int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+              9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+      double val = (n >= m) ? Ke[m][n] : Ke[n][m];
+      C[(int64_t)s * g.total + row] += val;
+    }
+  }
+}
+
+// sum_g dN_m(g) . (adj(J_g) v_g) for the 8 local nodes; v_g supplied by Vsrc.
+template <typename Vsrc>
+__device__ __forceinline__ void weak_div_elem(const Geo& G, int quad, const Vsrc& vsrc,
+                                              double out[8]) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) out[m] = 0.0;
+  const int ng = quad == 0 ? 8 : 1;
+#pragma unroll 1
+  for (int gp = 0; gp < ng; ++gp) {
+    double xi[3] = {0.0, 0.0, 0.0}, J[3][3], adj[3][3], v[3];
+    double wgt = 8.0;
+    if (quad == 0) { gauss_xi(gp, xi); wgt = 1.0; }
+    jacobian_at(G, xi, J);
+    adjugate(J, adj);
+    vsrc(gp, xi, v);
+    double w[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) w[r] = wgt * (adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2]);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      double dN[3];
+      dshape(m, xi, dN);
+      out[m] += dN[0] * w[0] + dN[1] * w[1] + dN[2] * w[2];
+    }
+  }
+}
+
+struct NodalInterp {
+  double ue[8][3];
+  __device__ void operator()(int, const double xi[3], double v[3]) const {
+    v[0] = v[1] = v[2] = 0.0;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      double N = shape(n, xi);
+      v[0] += N * ue[n][0];
+      v[1] += N * ue[n][1];
+      v[2] += N * ue[n][2];
+    }
+  }
+};
+
+struct GaussValues {
+  const double* ug;
+  int64_t e, NE;
+  __device__ void operator()(int gp, const double*, double v[3]) const {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] = ug[((int64_t)d * 8 + gp) * NE + e];
+  }
+};
+
+__device__ __forceinline__ void load_u(const double* u0, int64_t N, int nx1, int ny1, int i,
+                                       int j, int k, double ue[8][3]) {
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    int64_t id = sidx(nx1, ny1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+    ue[n][0] = u0[id];
+    ue[n][1] = u0[N + id];
+    ue[n][2] = u0[2 * N + id];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, int nz,
+                                                      const double* __restrict__ X,
+                                                      const double* __restrict__ Y,
+                                                      const double* __restrict__ Z,
+                                                      const double* __restrict__ u0, int quad,
+                                                      double* __restrict__ f, int cls) {
+  int i, j, k;
+  if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
+  Geo G;
+  load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+  NodalInterp src;
+  int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  load_u(u0, N, nx + 1, ny + 1, i, j, k, src.ue);
+  double fe[8];
+  weak_div_elem(G, quad, src, fe);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
+    if (!is_free(g, im, jm, km)) continue;
+    f[gidx(g, im, jm, km)] -= fe[m];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_weak_div(int nx, int ny, int nz,
+                                                  const double* __restrict__ X,
+                                                  const double* __restrict__ Y,
+                                                  const double* __restrict__ Z,
+                                                  const double* __restrict__ ug,
+                                                  double* __restrict__ out, int cls) {
+  int i, j, k;
+  if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
+  Geo G;
+  load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+  GaussValues src{ug, ((int64_t)k * ny + j) * nx + i, (int64_t)nx * ny * nz};
+  double be[8];
+  weak_div_elem(G, 0, src, be);
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+    out[sidx(nx + 1, ny + 1, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] += be[m];
+}
+
+__global__ void __launch_bounds__(128) k_recover(Grid g, int nx, int ny, int nz,
+                                                 const double* __restrict__ X,
+                                                 const double* __restrict__ Y,
+                                                 const double* __restrict__ Z,
+                                                 const double* __restrict__ u0,
+                                                 const double* __restrict__ lam, double d0,
+                                                 double d1, double d2, int where,
+                                                 double* __restrict__ u) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= nx || j >= ny || k >= nz) return;
+  Geo G;
+  load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+  double ue[8][3], le[8];
+  int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  load_u(u0, N, nx + 1, ny + 1, i, j, k, ue);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) le[n] = lam[gidx(g, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1))];
+  int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
+  const int ng = where == 0 ? 1 : 8;
+  const double dd[3] = {d0, d1, d2};
+#pragma unroll 1
+  for (int gp = 0; gp < ng; ++gp) {
+    double xi[3] = {0.0, 0.0, 0.0}, J[3][3], adj[3][3];
+    if (where != 0) gauss_xi(gp, xi);
+    jacobian_at(G, xi, J);
+    double det = adjugate(J, adj);
+    double gr[3] = {0.0, 0.0, 0.0}, up[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      double dN[3], N = shape(n, xi);
+      dshape(n, xi, dN);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) gr[r] += le[n] * dN[r];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) up[d] += N * ue[n][d];
+    }
+    double inv = 1.0 / det;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // grad lambda_d = sum_r (J^{-1})[r][d] * gr[r]
+      double gd = (adj[0][d] * gr[0] + adj[1][d] * gr[1] + adj[2][d] * gr[2]) * inv;
+      u[((int64_t)d * ng + gp) * NE + e] = up[d] + gd * dd[d];
+    }
+  }
+}
+
+dim3 elem_grid(int nx, int ny, int nz, int cls, dim3 blk) {
+  int ci = (nx - (cls & 1) + 1) / 2, cj = (ny - ((cls >> 1) & 1) + 1) / 2;
+  int ck = (nz - ((cls >> 2) & 1) + 1) / 2;
+  return dim3((ci + blk.x - 1) / blk.x, (cj + blk.y - 1) / blk.y, ck);
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_stencil(const Grid& g, int nx, int ny, int nz, const double* X,
+                                    const double* Y, const double* Z, const double* a,
+                                    double* C, int* flag, cudaStream_t st) {
+  dim3 blk(32, 4, 1);
+  for (int cls = 0; cls < 8; ++cls) {
+    dim3 grd = elem_grid(nx, ny, nz, cls, blk);
+    if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
+    k_assemble_stencil<<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, 1.0 / (a[0] * a[0]),
+                                            1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), C, flag,
+                                            cls); count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_rhs(const Grid& g, int nx, int ny, int nz, const double* X,
+                                const double* Y, const double* Z, const double* u0, int quad,
+                                double* f, cudaStream_t st) {
+  dim3 blk(32, 4, 1);
+  for (int cls = 0; cls < 8; ++cls) {
+    dim3 grd = elem_grid(nx, ny, nz, cls, blk);
+    if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
+    k_assemble_rhs<<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, quad, f, cls); count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weak_div(int nx, int ny, int nz, const double* X, const double* Y,
+                            const double* Z, const double* ug, double* out, cudaStream_t st) {
+  dim3 blk(32, 4, 1);
+  for (int cls = 0; cls < 8; ++cls) {
+    dim3 grd = elem_grid(nx, ny, nz, cls, blk);
+    if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
+    k_weak_div<<<grd, blk, 0, st>>>(nx, ny, nz, X, Y, Z, ug, out, cls); count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* X,
+                           const double* Y, const double* Z, const double* u0,
+                           const double* lam, const double* a, int where, double* u,
+                           cudaStream_t st) {
+  dim3 blk(32, 4, 1);
+  dim3 grd((nx + 31) / 32, (ny + 3) / 4, nz);
+  k_recover<<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, lam, 1.0 / (a[0] * a[0]),
+                                 1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), where, u); count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mcw

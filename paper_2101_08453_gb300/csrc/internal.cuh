@@ -1,0 +1,140 @@
+// Internal declarations of the mcwind CUDA library (sm_103a).
+//
+// Node arrays inside the workspace use a parity-split row layout: in each
+// row (fixed j, k) the even-i nodes come first, then the odd-i nodes, each
+// half padded to a multiple of 16 elements:
+//     idx(i, j, k) = k*PP + j*RP + (i & 1)*H + (i >> 1),   RP = 2H, PP = Ny*RP.
+// The smoother updates one column group (i mod 2, j mod 2) at a time, so a
+// warp over consecutive same-group columns reads the stencil planes with
+// unit stride instead of stride 2.
+//
+// A level's operator is stored as 28 planes of that layout: plane
+// s = (di+1) + 3(dj+1) + 9(dk+1) (s = 13 the diagonal) holds K_FF(n, n+d),
+// plane 27 holds 1/K(n, n).  Rows and columns of fixed (Dirichlet) nodes
+// are zero, so the planes hold exactly the free block K_FF of Eq. 5.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/mcwind.h"
+
+namespace mcw {
+
+constexpr int kPlanes = 28;
+constexpr int kDiag = 13;
+constexpr int kInvDiag = 27;
+constexpr int kMaxZ = 128;          // max node layers on any level
+constexpr int kMaxCoarse = 4096;    // max free unknowns of the dense coarsest solve
+
+// every kernel launch of the library is counted here (mcwind_launch_count)
+void count_launches(int n);
+
+struct Grid {
+  int Nx, Ny, Nz;
+  int H;          // half-row pitch (elements)
+  int64_t RP;     // row pitch = 2H
+  int64_t PP;     // layer pitch = Ny*RP
+  int64_t total;  // Nz*PP
+};
+
+inline Grid make_grid(int Nx, int Ny, int Nz) {
+  Grid g;
+  g.Nx = Nx; g.Ny = Ny; g.Nz = Nz;
+  int half = (Nx + 1) / 2;
+  g.H = (half + 15) / 16 * 16;
+  g.RP = 2 * (int64_t)g.H;
+  g.PP = (int64_t)Ny * g.RP;
+  g.total = (int64_t)Nz * g.PP;
+  return g;
+}
+
+__host__ __device__ inline int64_t gidx(const Grid& g, int i, int j, int k) {
+  return (int64_t)k * g.PP + (int64_t)j * g.RP + (int64_t)(i & 1) * g.H + (i >> 1);
+}
+
+__host__ __device__ inline bool is_free(const Grid& g, int i, int j, int k) {
+  return i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2 && k >= 0 && k <= g.Nz - 2;
+}
+
+// Transfer between level l (fine) and l+1 (coarse), passed by value.
+// Horizontal directions: coarse node I sits on fine node 2I, the last coarse
+// node on the last fine node; odd fine nodes interpolate half/half from
+// their two coarse neighbours (Sec. 3, the weights of trilinear
+// interpolation on a regular grid).  Vertical: kf[K] = fine layer of coarse
+// layer K (non-uniform after per-layer semicoarsening).
+struct Transfer {
+  int hx, hy;
+  int Nzf, Nzc;
+  int kf[kMaxZ];             // coarse K -> fine k
+  int kc0[kMaxZ], kc1[kMaxZ];  // fine k -> coarse layers (kc1 = kc0 when one)
+  double kw0[kMaxZ], kw1[kMaxZ];
+};
+
+// 1-D interpolation pair of a horizontal fine index f (Nf fine, Nc coarse nodes).
+__host__ __device__ inline void hpair(int coarsen, int Nf, int Nc, int f, int& c0, double& w0,
+                                      int& c1, double& w1) {
+  if (!coarsen) { c0 = c1 = f; w0 = 1.0; w1 = 0.0; return; }
+  if (f == Nf - 1) { c0 = c1 = Nc - 1; w0 = 1.0; w1 = 0.0; return; }
+  if ((f & 1) == 0) { c0 = c1 = f >> 1; w0 = 1.0; w1 = 0.0; return; }
+  c0 = (f - 1) >> 1; c1 = (f + 1) >> 1; w0 = 0.5; w1 = 0.5;
+  if (f + 1 == Nf - 1) c1 = Nc - 1;
+}
+
+// Fine node of horizontal coarse index I and the weights of its fine
+// neighbours f-1 and f+1 in the restriction.
+__host__ __device__ inline void hcoarse(int coarsen, int Nf, int Nc, int I, int& f, double& wm,
+                                        double& wp) {
+  if (!coarsen) { f = I; wm = wp = 0.0; return; }
+  f = (I == Nc - 1) ? Nf - 1 : 2 * I;
+  wm = (f >= 1 && ((f - 1) & 1)) ? 0.5 : 0.0;
+  wp = (f + 1 <= Nf - 2 && ((f + 1) & 1)) ? 0.5 : 0.0;
+}
+
+struct Level {
+  Grid g;
+  int n_free;
+  // device pointers into the workspace
+  double* C64 = nullptr;   // kPlanes * g.total
+  float* C32 = nullptr;
+  double *x64 = nullptr, *f64 = nullptr, *r64 = nullptr;
+  float *x32 = nullptr, *f32 = nullptr, *r32 = nullptr;
+  // host description of the transfer to the next level
+  int hx = 0, hy = 0;
+  std::vector<int> kmap;   // coarse layer -> fine layer
+  Transfer tr;
+};
+
+}  // namespace mcw
+
+struct mcwind_plan_s {
+  int nx, ny, nz;
+  double a[3];
+  mcwind_options opt;
+  std::vector<mcw::Level> lv;
+  // workspace layout (byte offsets) and sizes
+  size_t ws_bytes = 0;
+  size_t off_tmp = 0, tmp_bytes = 0;        // RAP intermediates, layout conversion
+  size_t off_dense = 0;                     // coarsest inverse n_c x n_c, plus scratch
+  size_t off_partials = 0;                  // reduction partials
+  size_t off_scalars = 0;                   // device scalars / flags
+  size_t off_cfree = 0;                     // coarsest free-node grid indices
+  int n_coarse = 0;
+  int n_partials = 0;
+  // bound at assemble
+  char* ws = nullptr;
+  const double *X = nullptr, *Y = nullptr, *Z = nullptr;
+  bool assembled = false;
+  // profiler: event pairs recorded around kernel classes while enabled
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, int>> prof_marks;  // (kind, launches) per event pair
+  double prof_ms[MCWIND_K_KINDS] = {0};
+  long long prof_n[MCWIND_K_KINDS] = {0};
+  // per-plan CUDA objects
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t cycle_graph[2] = {nullptr, nullptr};
+  cudaEvent_t ev = nullptr;
+};

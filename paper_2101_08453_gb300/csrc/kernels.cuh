@@ -1,0 +1,84 @@
+// Launch wrappers of the mcwind kernels (each returns the launch status).
+#pragma once
+#include "internal.cuh"
+
+namespace mcw {
+
+// ---- element.cu: isoparametric trilinear hexahedra (Sec. 2) ----
+// Stiffness (Eq. 5 left side, 2x2x2 Gauss) scattered into the 28-plane
+// stencil of level 0 (planes must be zero on entry); flag |= 1 on detJ <= 0.
+cudaError_t launch_assemble_stencil(const Grid& g, int nx, int ny, int nz, const double* X,
+                                    const double* Y, const double* Z, const double* a,
+                                    double* C, int* flag, cudaStream_t st);
+// Load vector (Eq. 5 right side) into f (split layout, zero on entry).
+cudaError_t launch_assemble_rhs(const Grid& g, int nx, int ny, int nz, const double* X,
+                                const double* Y, const double* Z, const double* u0, int quad,
+                                double* f, cudaStream_t st);
+// u = u0 + A^{-1} grad lambda (Eq. 3); lambda in split layout.
+cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* X,
+                           const double* Y, const double* Z, const double* u0,
+                           const double* lam, const double* a, int where, double* u,
+                           cudaStream_t st);
+// (B u)_m at every node, out in standard layout, zero on entry.
+cudaError_t launch_weak_div(int nx, int ny, int nz, const double* X, const double* Y,
+                            const double* Z, const double* ug, double* out, cudaStream_t st);
+
+// ---- layout.cu ----
+template <typename T>
+cudaError_t launch_std_to_split(const Grid& g, const double* src, T* dst, bool zero_fixed,
+                                cudaStream_t st);
+template <typename T>
+cudaError_t launch_split_to_std(const Grid& g, const T* src, double* dst, cudaStream_t st);
+// planes of the split layout -> [27][Nz][Ny][Nx] standard layout (float64)
+template <typename T>
+cudaError_t launch_stencil_export(const Grid& g, const T* C, double* out, cudaStream_t st);
+cudaError_t launch_stencil_to_f32(const Grid& g, const double* C64, float* C32, cudaStream_t st);
+// zero couplings to fixed nodes, rows of fixed nodes, set plane 27 = 1/diag;
+// flag |= 2 if a free diagonal is not positive.
+cudaError_t launch_stencil_finalize(const Grid& g, double* C, int* flag, cudaStream_t st);
+// sum of n partials in fixed order -> *out
+cudaError_t launch_reduce_final(const double* partials, int n, double* out, cudaStream_t st);
+// sum over free nodes of v^2 (split layout) -> partials; returns block count via *nblocks
+cudaError_t launch_norm2_partials(const Grid& g, const double* v, double* partials, int* nblocks,
+                                  cudaStream_t st);
+
+// ---- smooth.cu: vertical Gauss-Seidel, one column group (Sec. 3) ----
+template <typename T>
+cudaError_t launch_gs_group(const Grid& g, const T* C, const T* f, T* x, int group, int up,
+                            cudaStream_t st);
+
+// ---- transfer.cu ----
+// r = f - K x at free nodes (0 elsewhere); partials of sum r^2 if partials != nullptr
+template <typename T>
+cudaError_t launch_residual(const Grid& g, const T* C, const T* f, const T* x, T* r,
+                            double* partials, int* nblocks, cudaStream_t st);
+// mixed refinement: r64 = f - K64 x64; r32 = (float) r64; e32 = 0; partials of r64^2
+cudaError_t launch_residual_mixed(const Grid& g, const double* C, const double* f,
+                                  const double* x, float* r32, float* e32, double* partials,
+                                  int* nblocks, cudaStream_t st);
+// x64 += e32 at free nodes
+cudaError_t launch_update_mixed(const Grid& g, double* x, const float* e, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const Transfer& tr, const T* r,
+                            T* fc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const Transfer& tr, const T* ec,
+                               T* x, cudaStream_t st);
+int residual_blocks(const Grid& g);
+
+// ---- rap.cu: K_c = P^T K P one direction at a time (Eq. 7) ----
+// dim 0/1: horizontal coarsening of x/y; dim 2: vertical with tr's layer map.
+cudaError_t launch_rap_stage(int dim, const Grid& gin, const Grid& gout, const Transfer& tr,
+                             const double* Sin, double* Sout, cudaStream_t st);
+
+// ---- coarse.cu: dense direct solve on the coarsest level ----
+cudaError_t launch_coarse_index(const Grid& g, int* cfree, cudaStream_t st);
+cudaError_t launch_dense_gather(const Grid& g, const double* C, const int* cfree, int n,
+                                double* A, cudaStream_t st);
+// Gauss-Jordan inversion, n steps ping-ponging between A and B; result in *result
+cudaError_t launch_dense_invert(double* A, double* B, int n, double** result, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dense_solve(const double* Ainv, int n, const int* cfree, const T* f, T* x,
+                               cudaStream_t st);
+
+}  // namespace mcw

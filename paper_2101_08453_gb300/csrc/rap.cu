@@ -1,0 +1,105 @@
+// Galerkin coarse operator K_c = P^T K P (Eq. 7, second row).
+//
+// P is a tensor product P = Pz (x) Py (x) Px of 1-D interpolations, so
+//   P^T K P = Pz^T (Py^T (Px^T K Px) Py) Pz
+// and the product is formed one direction at a time.  Each stage maps a
+// 27-point operator on one grid to a 27-point operator on a grid coarsened
+// in one direction:
+//   S'(I; D, e) = sum_{a} sum_{d} P(f_I + a, I) S(f_I + a; d, e) P(f_I + a + d, I + D)
+// (a, d, D in {-1, 0, 1}; e the offsets in the other two directions,
+// unchanged).  One thread computes the 27 entries of one output node from
+// the 3 x 27 input entries it depends on.
+#include "kernels.cuh"
+
+namespace mcw {
+namespace {
+
+__device__ __forceinline__ bool node_of_thread(const Grid& g, int& i, int& j, int& k) {
+  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  j = blockIdx.y * blockDim.y + threadIdx.y;
+  k = blockIdx.z >> 1;
+  i = 2 * h + (blockIdx.z & 1);
+  return i < g.Nx && j < g.Ny;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_rap(Grid gin, Grid gout, Transfer tr,
+                                             const double* __restrict__ Sin,
+                                             double* __restrict__ Sout) {
+  int i, j, k;
+  if (!node_of_thread(gout, i, j, k)) return;
+  const int Iout = DIM == 0 ? i : (DIM == 1 ? j : k);
+  const int Nf = DIM == 0 ? gin.Nx : (DIM == 1 ? gin.Ny : gin.Nz);
+  const int Nc = DIM == 0 ? gout.Nx : (DIM == 1 ? gout.Ny : gout.Nz);
+  int f;
+  double wa[3];
+  if (DIM < 2) {
+    hcoarse(1, Nf, Nc, Iout, f, wa[0], wa[2]);
+  } else {
+    f = tr.kf[Iout];
+    wa[0] = (Iout > 0 && tr.kf[Iout] - tr.kf[Iout - 1] == 2) ? 0.5 : 0.0;
+    wa[2] = (Iout < tr.Nzc - 1 && tr.kf[Iout + 1] - tr.kf[Iout] == 2) ? 0.5 : 0.0;
+  }
+  wa[1] = 1.0;
+  // Pw[q][D] = P(f + q - 2, Iout + D - 1)
+  double Pw[5][3];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int b = f + q - 2;
+    int c0 = -100, c1 = -100;
+    double w0 = 0.0, w1 = 0.0;
+    if (b >= 0 && b <= Nf - 1) {
+      if (DIM < 2) {
+        hpair(1, Nf, Nc, b, c0, w0, c1, w1);
+      } else {
+        c0 = tr.kc0[b]; c1 = tr.kc1[b]; w0 = tr.kw0[b]; w1 = tr.kw1[b];
+      }
+    }
+#pragma unroll
+    for (int D = 0; D < 3; ++D) {
+      const int J = Iout + D - 1;
+      Pw[q][D] = (c0 == J ? w0 : 0.0) + (c1 == J && c1 != c0 ? w1 : 0.0);
+    }
+  }
+  double out[27];
+#pragma unroll
+  for (int s = 0; s < 27; ++s) out[s] = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (wa[a] == 0.0) continue;
+    const int ii = DIM == 0 ? f + a - 1 : i;
+    const int jj = DIM == 1 ? f + a - 1 : j;
+    const int kk = DIM == 2 ? f + a - 1 : k;
+    const int64_t in = gidx(gin, ii, jj, kk);
+#pragma unroll
+    for (int s = 0; s < 27; ++s) {
+      const int di = s % 3, dj = (s / 3) % 3, dk = s / 9;  // 0..2
+      const int d = DIM == 0 ? di : (DIM == 1 ? dj : dk);
+      const double v = wa[a] * Sin[(int64_t)s * gin.total + in];
+#pragma unroll
+      for (int D = 0; D < 3; ++D) {
+        const int so = DIM == 0 ? D + 3 * dj + 9 * dk
+                                : (DIM == 1 ? di + 3 * D + 9 * dk : di + 3 * dj + 9 * D);
+        out[so] += v * Pw[a + d][D];
+      }
+    }
+  }
+  const int64_t o = gidx(gout, i, j, k);
+#pragma unroll
+  for (int s = 0; s < 27; ++s) Sout[(int64_t)s * gout.total + o] = out[s];
+}
+
+}  // namespace
+
+cudaError_t launch_rap_stage(int dim, const Grid& gin, const Grid& gout, const Transfer& tr,
+                             const double* Sin, double* Sout, cudaStream_t st) {
+  dim3 grd((gout.H + 31) / 32, (gout.Ny + 3) / 4, 2 * gout.Nz);
+  dim3 blk(32, 4);
+  if (dim == 0) k_rap<0><<<grd, blk, 0, st>>>(gin, gout, tr, Sin, Sout);
+  else if (dim == 1) k_rap<1><<<grd, blk, 0, st>>>(gin, gout, tr, Sin, Sout);
+  else k_rap<2><<<grd, blk, 0, st>>>(gin, gout, tr, Sin, Sout);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mcw

@@ -1,0 +1,229 @@
+// Residual, restriction and prolongation (Sec. 3, Eq. 7), and the float64
+// refinement kernels of the mixed-precision solve.
+#include "kernels.cuh"
+
+namespace mcw {
+namespace {
+
+constexpr int kResThreads = 128;
+
+// Sum over the block in fixed order; thread 0 writes the block's partial.
+__device__ __forceinline__ void block_partial(double s, double* partials) {
+  __shared__ double red[kResThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((t & 31) == 0) red[t >> 5] = s;
+  __syncthreads();
+  if (t == 0) {
+    double b = 0.0;
+#pragma unroll
+    for (int q = 0; q < kResThreads / 32; ++q) b += red[q];
+    partials[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
+  }
+}
+
+// r = f - K x over one column, all k, both parities (blockIdx.z = parity).
+// MODE 0: write r (type T).  MODE 1 (T = double): write (float) r into r32
+// and zero e32, the start of one float32 correction cycle.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __restrict__ C,
+                                                          const T* __restrict__ f,
+                                                          const T* __restrict__ x,
+                                                          T* __restrict__ r,
+                                                          float* __restrict__ r32,
+                                                          float* __restrict__ e32,
+                                                          double* __restrict__ partials) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = 2 * h + (int)blockIdx.z;
+  double ss = 0.0;
+  if (i < g.Nx && j < g.Ny) {
+    const int64_t PP = g.PP, tot = g.total;
+    const int64_t own = (int64_t)j * g.RP + (int64_t)(i & 1) * g.H + (i >> 1);
+    const bool fcol = i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2;
+    if (!fcol) {
+      for (int k = 0; k < g.Nz; ++k) {
+        const int64_t b = (int64_t)k * PP + own;
+        if (MODE == 0) r[b] = T(0);
+        else { r32[b] = 0.0f; e32[b] = 0.0f; }
+      }
+    } else {
+      int64_t col[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const int ii = i + c % 3 - 1, jj = j + c / 3 - 1;
+        col[c] = (int64_t)jj * g.RP + (int64_t)(ii & 1) * g.H + (ii >> 1);
+      }
+      T w[3][9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        w[0][c] = T(0);
+        w[1][c] = x[col[c]];
+        w[2][c] = x[PP + col[c]];
+      }
+      for (int k = 0; k <= g.Nz - 2; ++k) {
+        const int64_t b = (int64_t)k * PP + own;
+        T acc = f[b];
+#pragma unroll
+        for (int s = 0; s < 27; ++s) acc -= C[s * tot + b] * w[s / 9][s % 9];
+        ss += (double)acc * (double)acc;
+        if (MODE == 0) r[b] = acc;
+        else { r32[b] = (float)acc; e32[b] = 0.0f; }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          w[0][c] = w[1][c];
+          w[1][c] = w[2][c];
+        }
+        if (k + 2 <= g.Nz - 1) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) w[2][c] = x[(int64_t)(k + 2) * PP + col[c]];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) w[2][c] = T(0);
+        }
+      }
+      const int64_t b = (int64_t)(g.Nz - 1) * PP + own;
+      if (MODE == 0) r[b] = T(0);
+      else { r32[b] = 0.0f; e32[b] = 0.0f; }
+    }
+  }
+  if (partials) block_partial(ss, partials);
+}
+
+__device__ __forceinline__ bool node_of_thread(const Grid& g, int& i, int& j, int& k) {
+  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  j = blockIdx.y * blockDim.y + threadIdx.y;
+  k = blockIdx.z >> 1;
+  i = 2 * h + (blockIdx.z & 1);
+  return i < g.Nx && j < g.Ny;
+}
+
+inline dim3 node_grid(const Grid& g) { return dim3((g.H + 31) / 32, (g.Ny + 3) / 4, 2 * g.Nz); }
+
+__global__ void k_update_mixed(Grid g, double* __restrict__ x, const float* __restrict__ e) {
+  int i, j, k;
+  if (!node_of_thread(g, i, j, k) || !is_free(g, i, j, k)) return;
+  const int64_t b = gidx(g, i, j, k);
+  x[b] += (double)e[b];
+}
+
+// vertical restriction weights of coarse layer K
+__device__ __forceinline__ void vcoarse(const Transfer& tr, int K, int& f, double& wm, double& wp) {
+  f = tr.kf[K];
+  wm = (K > 0 && tr.kf[K] - tr.kf[K - 1] == 2) ? 0.5 : 0.0;
+  wp = (K < tr.Nzc - 1 && tr.kf[K + 1] - tr.kf[K] == 2) ? 0.5 : 0.0;
+}
+
+template <typename T>
+__global__ void k_restrict(Grid gf, Grid gc, Transfer tr, const T* __restrict__ r,
+                           T* __restrict__ fc) {
+  int I, J, K;
+  if (!node_of_thread(gc, I, J, K)) return;
+  const int64_t out = gidx(gc, I, J, K);
+  if (!is_free(gc, I, J, K)) { fc[out] = T(0); return; }
+  int fi, fj, fk;
+  double wx[3], wy[3], wz[3];
+  hcoarse(tr.hx, gf.Nx, gc.Nx, I, fi, wx[0], wx[2]);
+  hcoarse(tr.hy, gf.Ny, gc.Ny, J, fj, wy[0], wy[2]);
+  vcoarse(tr, K, fk, wz[0], wz[2]);
+  wx[1] = wy[1] = wz[1] = 1.0;
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (wz[c] == 0.0) continue;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (wy[b] == 0.0) continue;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (wx[a] == 0.0) continue;
+        s += wx[a] * wy[b] * wz[c] * (double)r[gidx(gf, fi + a - 1, fj + b - 1, fk + c - 1)];
+      }
+    }
+  }
+  fc[out] = (T)s;
+}
+
+template <typename T>
+__global__ void k_prolong_add(Grid gf, Grid gc, Transfer tr, const T* __restrict__ ec,
+                              T* __restrict__ x) {
+  int i, j, k;
+  if (!node_of_thread(gf, i, j, k) || !is_free(gf, i, j, k)) return;
+  int ci[2], cj[2], ck[2];
+  double wx[2], wy[2], wz[2];
+  hpair(tr.hx, gf.Nx, gc.Nx, i, ci[0], wx[0], ci[1], wx[1]);
+  hpair(tr.hy, gf.Ny, gc.Ny, j, cj[0], wy[0], cj[1], wy[1]);
+  ck[0] = tr.kc0[k]; ck[1] = tr.kc1[k]; wz[0] = tr.kw0[k]; wz[1] = tr.kw1[k];
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (wz[c] == 0.0) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (wy[b] == 0.0) continue;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        if (wx[a] == 0.0) continue;
+        s += wx[a] * wy[b] * wz[c] * (double)ec[gidx(gc, ci[a], cj[b], ck[c])];
+      }
+    }
+  }
+  const int64_t o = gidx(gf, i, j, k);
+  x[o] = (T)((double)x[o] + s);
+}
+
+}  // namespace
+
+int residual_blocks(const Grid& g) {
+  return ((g.H + 31) / 32) * ((g.Ny + 3) / 4) * 2;
+}
+
+template <typename T>
+cudaError_t launch_residual(const Grid& g, const T* C, const T* f, const T* x, T* r,
+                            double* partials, int* nblocks, cudaStream_t st) {
+  dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
+  k_residual<T, 0><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, partials); count_launches(1);
+  if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+  return cudaGetLastError();
+}
+template cudaError_t launch_residual<double>(const Grid&, const double*, const double*,
+                                             const double*, double*, double*, int*, cudaStream_t);
+template cudaError_t launch_residual<float>(const Grid&, const float*, const float*,
+                                            const float*, float*, double*, int*, cudaStream_t);
+
+cudaError_t launch_residual_mixed(const Grid& g, const double* C, const double* f,
+                                  const double* x, float* r32, float* e32, double* partials,
+                                  int* nblocks, cudaStream_t st) {
+  dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
+  k_residual<double, 1><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, nullptr, r32, e32, partials); count_launches(1);
+  if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_mixed(const Grid& g, double* x, const float* e, cudaStream_t st) {
+  k_update_mixed<<<node_grid(g), dim3(32, 4), 0, st>>>(g, x, e); count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const Transfer& tr, const T* r,
+                            T* fc, cudaStream_t st) {
+  k_restrict<T><<<node_grid(gc), dim3(32, 4), 0, st>>>(gf, gc, tr, r, fc); count_launches(1);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const Transfer& tr, const T* ec,
+                               T* x, cudaStream_t st) {
+  k_prolong_add<T><<<node_grid(gf), dim3(32, 4), 0, st>>>(gf, gc, tr, ec, x); count_launches(1);
+  return cudaGetLastError();
+}
+template cudaError_t launch_restrict<double>(const Grid&, const Grid&, const Transfer&,
+                                             const double*, double*, cudaStream_t);
+template cudaError_t launch_restrict<float>(const Grid&, const Grid&, const Transfer&,
+                                            const float*, float*, cudaStream_t);
+template cudaError_t launch_prolong_add<double>(const Grid&, const Grid&, const Transfer&,
+                                                const double*, double*, cudaStream_t);
+template cudaError_t launch_prolong_add<float>(const Grid&, const Grid&, const Transfer&,
+                                               const float*, float*, cudaStream_t);
+
+}  // namespace mcw

@@ -215,6 +215,36 @@ def full_domain(nx=3000, ny=3000, nz=15, seed=0, a=(1.0, 1.0, 1.0), dx=DX,
                 layer_thicknesses(nz), {"theta": theta})
 
 
+def full_domain_window(i0, j0, w, h, nx=3000, ny=3000, nz=15, seed=0, a=(1.0, 1.0, 1.0),
+                       dx=DX, coarse=100) -> Case:
+    """Cells [i0, i0+w) x [j0, j0+h) of full_domain(nx, ny, nz, seed): the
+    same terrain, wind and node positions, cut out as a w x h x nz problem
+    (its lateral faces become fixed boundaries)."""
+    rng = np.random.default_rng(seed)
+    zs = ridge_terrain(nx, ny, rng, dx)
+    theta = rng.uniform(0.0, 360.0)
+    th = math.radians(theta)
+    means = np.linspace(5.0, 15.0, nz)
+    cu = -means[:, None, None] * math.sin(th) + rng.normal(0.0, 2.0, (nz, coarse, coarse))
+    cv = -means[:, None, None] * math.cos(th) + rng.normal(0.0, 2.0, (nz, coarse, coarse))
+    Wy = _bilinear_matrix(ny + 1, coarse)[j0:j0 + h + 1]
+    Wx = _bilinear_matrix(nx + 1, coarse)[i0:i0 + w + 1]
+    zeta = zeta_levels(nz)
+    shape = (nz + 1, h + 1, w + 1)
+    Z = zs[None, j0:j0 + h + 1, i0:i0 + w + 1] + zeta[:, None, None]
+    x = dx * np.arange(i0, i0 + w + 1, dtype=np.float64)
+    y = dx * np.arange(j0, j0 + h + 1, dtype=np.float64)
+    X = np.broadcast_to(x[None, None, :], shape).copy()
+    Y = np.broadcast_to(y[None, :, None], shape).copy()
+    u0 = np.zeros((3,) + shape)
+    for k in range(nz + 1):
+        kc = min(k, nz - 1)
+        u0[0, k] = Wy @ cu[kc] @ Wx.T
+        u0[1, k] = Wy @ cv[kc] @ Wx.T
+    return Case(f"window{w}x{h}x{nz}@{i0},{j0}", w, h, nz, tuple(a), X, Y,
+                np.ascontiguousarray(Z), u0, dx, layer_thicknesses(nz), {"theta": theta})
+
+
 def perturb_wind(u0: np.ndarray, seed: int, rel: float = 0.02) -> np.ndarray:
     """The next time step's first guess: u0 * (1 + rel * xi), xi ~ N(0, 1)."""
     rng = np.random.default_rng(seed + 1000003)

@@ -1,0 +1,117 @@
+"""Host-side checks of the C library (no GPU needed): it loads, exports every
+entry point its header declares, rejects bad arguments, and its planner
+reproduces the semicoarsening hierarchy of Sec. 3 as the oracle plans it."""
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_2101_08453_gb300 as m
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    m.build.build()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "mcwind.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcwind_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    L = m.lib()
+    syms = declared_symbols()
+    assert len(syms) >= 19
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_strerror_names_codes():
+    L = m.lib()
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert L.mcwind_strerror(code)
+    assert L.mcwind_strerror(-2) != L.mcwind_strerror(-3)
+
+
+@pytest.mark.parametrize("args", [
+    dict(nx=1, ny=4, nz=3), dict(nx=4, ny=1, nz=3), dict(nx=4, ny=4, nz=0),
+    dict(nx=4, ny=4, nz=200),
+])
+def test_plan_rejects_bad_sizes(args):
+    with pytest.raises(m.MCWindError) as e:
+        m.mcwind_plan_create(args["nx"], args["ny"], args["nz"], (1, 1, 1), 30.0,
+                             [5.0] * max(1, args["nz"]))
+    assert e.value.code == m.MCWIND_EINVAL
+
+
+@pytest.mark.parametrize("bad", [
+    dict(a=(0, 1, 1)), dict(a=(1, -1, 1)), dict(h1=0.0), dict(h3=[5, 0, 5]),
+    dict(opt=dict(precision=3)), dict(opt=dict(nu_pre=0, nu_post=0)),
+    dict(opt=dict(coarsest_max=0)), dict(opt=dict(coarsest_max=100000)),
+    dict(opt=dict(coarsen_rule=7)), dict(opt=dict(rhs_quad=2)),
+])
+def test_plan_rejects_bad_options(bad):
+    a = bad.get("a", (1, 1, 1))
+    h1 = bad.get("h1", 30.0)
+    h3 = bad.get("h3", [5.0, 6.0, 7.0])
+    o = m.default_options(**bad.get("opt", {}))
+    with pytest.raises(m.MCWindError) as e:
+        m.mcwind_plan_create(8, 8, 3, a, h1, h3, o)
+    assert e.value.code == m.MCWIND_EINVAL
+
+
+def test_null_pointer_entry_points_return_einval():
+    L = m.lib()
+    h, _ = m.mcwind_plan_create(8, 8, 3, (1, 1, 1), 30.0, [5.0, 6.0, 7.0])
+    try:
+        assert L.mcwind_assemble(h, None, None, None, None, None) == m.MCWIND_EINVAL
+        assert L.mcwind_solve(h, None, None, 1e-8, 10, 0, None, None) == m.MCWIND_EINVAL
+        assert L.mcwind_recover(h, None, None, None, 0, None) == m.MCWIND_EINVAL
+        assert L.mcwind_solve(None, None, None, 1e-8, 10, 0, None, None) == m.MCWIND_EINVAL
+        # not assembled yet: state error, not a CUDA call
+        import ctypes
+        p = ctypes.c_void_p(256)
+        assert L.mcwind_solve(h, p, p, 1e-8, 10, 0, None, None) == m.MCWIND_ESTATE
+        assert L.mcwind_level_smooth(h, 0, 0, p, p, 1, 0, None) == m.MCWIND_ESTATE
+    finally:
+        m.mcwind_plan_destroy(h)
+
+
+CASES = [
+    ("hill64", lambda: synth.single_hill(), (1, 1, 1), 0, 1024),
+    ("hills512", lambda: synth.single_hill(512, 512, 16), (1, 1, 1), 0, 1024),
+    ("hills512_a10_paper", lambda: synth.single_hill(512, 512, 16), (1, 1, 10), 0, 1024),
+    ("hills512_a10_op", lambda: synth.single_hill(512, 512, 16), (1, 1, 10), 1, 1024),
+    ("odd", lambda: synth.single_hill(37, 23, 7), (1, 1, 1), 0, 16),
+    ("odd_a4", lambda: synth.single_hill(45, 61, 13), (1, 2, 4), 1, 64),
+    ("thick", lambda: synth.flat_box(40, 40, 5, dz=200.0, stretch=1.0), (1, 1, 1), 0, 32),
+]
+
+
+@pytest.mark.parametrize("name,maker,a,rule,cmax", CASES, ids=[c[0] for c in CASES])
+def test_planner_matches_oracle(name, maker, a, rule, cmax):
+    c = maker()
+    ref = oracle.plan_levels(c.nx, c.ny, c.nz, c.h1, c.h3, a, "paper" if rule == 0 else "operator", cmax)
+    plan = m.Plan(c.nx, c.ny, c.nz, a, c.h1, c.h3, coarsen_rule=rule, coarsest_max=cmax)
+    assert plan.num_levels == len(ref)
+    for l, want in enumerate(ref):
+        got = plan.level(l)
+        for key in ("Nx", "Ny", "Nz", "hx", "hy", "kmap"):
+            if key in want:
+                assert got[key] == want[key], (l, key, got, want)
+
+
+def test_full_domain_hierarchy_shape():
+    h3 = synth.layer_thicknesses(15)
+    plan = m.Plan(3000, 3000, 15, (1, 1, 1), 30.0, h3, precision=m.PREC_MIXED)
+    ref = oracle.plan_levels(3000, 3000, 15, 30.0, h3, (1, 1, 1))
+    assert plan.num_levels == len(ref)
+    last = plan.level(plan.num_levels - 1)
+    assert (last["Nx"] - 2) * (last["Ny"] - 2) * (last["Nz"] - 1) <= 1024
+    assert plan.workspace_bytes < 150e9
