@@ -141,7 +141,7 @@ int vcycle(mcwind_plan p, int l, cudaStream_t st) {
   CKR(smooth<T>(p, l, p->opt.nu_pre, MCWIND_FORWARD, st));
   {
     PROF(l == 0 ? MCWIND_K_RESIDUAL_FINE : MCWIND_K_RESIDUAL_COARSE);
-    CK(launch_residual<T>(L.g, P.C, P.f, P.x, P.r, nullptr, nullptr, st));
+    CK(launch_residual<T>(L.g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
   }
   auto Q = Sel<T>::get(p, l + 1);
   {
@@ -170,7 +170,7 @@ int check_level(mcwind_plan p, int level, int precision) {
 int norm2(mcwind_plan p, const Grid& g, const double* v, int slot, cudaStream_t st) {
   PROF(MCWIND_K_OTHER);
   int nb = 0;
-  CK(launch_norm2_partials(g, v, partials(p), &nb, st));
+  CK(launch_norm2_partials(g, v, partials(p), p->n_partials, &nb, st));
   CK(launch_reduce_final(partials(p), nb, scal(p) + slot, st));
   return MCWIND_OK;
 }
@@ -183,10 +183,10 @@ int outer_residual(mcwind_plan p, cudaStream_t st) {
   int nb = 0;
   PROF(MCWIND_K_OUTER_RESIDUAL);
   if (p->opt.precision == MCWIND_PREC_F64) {
-    CK(launch_residual<double>(g, A.C, A.f, A.x, A.r, partials(p), &nb, st));
+    CK(launch_residual<double>(g, A.C, A.f, A.x, A.r, partials(p), p->n_partials, &nb, st));
   } else {
     Ptr32 B = lv32(p, 0);
-    CK(launch_residual_mixed(g, A.C, A.f, A.x, B.f, B.x, partials(p), &nb, st));
+    CK(launch_residual_mixed(g, A.C, A.f, A.x, B.f, B.x, partials(p), p->n_partials, &nb, st));
   }
   CK(launch_reduce_final(partials(p), nb, scal(p) + 1, st));
   return MCWIND_OK;
@@ -435,13 +435,13 @@ extern "C" int mcwind_level_residual(mcwind_plan p, int level, int precision, co
     Ptr64 P = lv64(p, level);
     CK(launch_std_to_split<double>(g, x, P.x, true, st));
     CK(launch_std_to_split<double>(g, f, P.f, true, st));
-    CK(launch_residual<double>(g, P.C, P.f, P.x, P.r, nullptr, nullptr, st));
+    CK(launch_residual<double>(g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
     CK(launch_split_to_std<double>(g, P.r, r, st));
   } else {
     Ptr32 P = lv32(p, level);
     CK(launch_std_to_split<float>(g, x, P.x, true, st));
     CK(launch_std_to_split<float>(g, f, P.f, true, st));
-    CK(launch_residual<float>(g, P.C, P.f, P.x, P.r, nullptr, nullptr, st));
+    CK(launch_residual<float>(g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
     CK(launch_split_to_std<float>(g, P.r, r, st));
   }
   return MCWIND_OK;

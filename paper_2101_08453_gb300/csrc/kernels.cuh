@@ -38,9 +38,10 @@ cudaError_t launch_stencil_to_f32(const Grid& g, const double* C64, float* C32, 
 cudaError_t launch_stencil_finalize(const Grid& g, double* C, int* flag, cudaStream_t st);
 // sum of n partials in fixed order -> *out
 cudaError_t launch_reduce_final(const double* partials, int n, double* out, cudaStream_t st);
-// sum over free nodes of v^2 (split layout) -> partials; returns block count via *nblocks
-cudaError_t launch_norm2_partials(const Grid& g, const double* v, double* partials, int* nblocks,
-                                  cudaStream_t st);
+// sum over free nodes of v^2 (split layout) -> residual_blocks(g) partials
+// (refuses to launch when that exceeds cap); block count via *nblocks
+cudaError_t launch_norm2_partials(const Grid& g, const double* v, double* partials, int cap,
+                                  int* nblocks, cudaStream_t st);
 
 // ---- smooth.cu: vertical Gauss-Seidel, one column group (Sec. 3) ----
 template <typename T>
@@ -49,13 +50,14 @@ cudaError_t launch_gs_group(const Grid& g, const T* C, const T* f, T* x, int gro
 
 // ---- transfer.cu ----
 // r = f - K x at free nodes (0 elsewhere); partials of sum r^2 if partials != nullptr
+// (residual_blocks(g) of them; refuses to launch when that exceeds cap)
 template <typename T>
 cudaError_t launch_residual(const Grid& g, const T* C, const T* f, const T* x, T* r,
-                            double* partials, int* nblocks, cudaStream_t st);
+                            double* partials, int cap, int* nblocks, cudaStream_t st);
 // mixed refinement: r64 = f - K64 x64; r32 = (float) r64; e32 = 0; partials of r64^2
 cudaError_t launch_residual_mixed(const Grid& g, const double* C, const double* f,
                                   const double* x, float* r32, float* e32, double* partials,
-                                  int* nblocks, cudaStream_t st);
+                                  int cap, int* nblocks, cudaStream_t st);
 // x64 += e32 at free nodes
 cudaError_t launch_update_mixed(const Grid& g, double* x, const float* e, cudaStream_t st);
 template <typename T>

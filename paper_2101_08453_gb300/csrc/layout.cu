@@ -68,27 +68,34 @@ __global__ void k_finalize(Grid g, double* __restrict__ C, int* flag) {
   C[kInvDiag * g.total + id] = fr ? 1.0 / d : 0.0;
 }
 
-constexpr int kRedThreads = 256;
+constexpr int kRedThreads = 128;
 
+// sum of v^2 over the free nodes: one thread per column (blockDim 32 x 4,
+// blockIdx.z = parity of i), the same launch shape as the residual kernel,
+// so it writes exactly residual_blocks(g) partials.
 __global__ void __launch_bounds__(kRedThreads) k_norm2_partials(Grid g, const double* __restrict__ v,
                                                                 double* __restrict__ partials) {
-  int i, j, k;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = 2 * h + (int)blockIdx.z;
   double s = 0.0;
-  if (node_of_thread(g, i, j, k) && is_free(g, i, j, k)) {
-    double x = v[gidx(g, i, j, k)];
-    s = x * x;
+  if (i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2) {
+    const int64_t own = (int64_t)j * g.RP + (int64_t)(i & 1) * g.H + (i >> 1);
+    for (int k = 0; k <= g.Nz - 2; ++k) {
+      const double x = v[(int64_t)k * g.PP + own];
+      s += x * x;
+    }
   }
   __shared__ double red[kRedThreads / 32];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-  int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-  if (lane == 0) red[warp] = s;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((t & 31) == 0) red[t >> 5] = s;
   __syncthreads();
-  if (warp == 0) {
-    s = lane < (int)(blockDim.x * blockDim.y / 32) ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0)
-      partials[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+  if (t == 0) {
+    double b = 0.0;
+#pragma unroll
+    for (int q = 0; q < kRedThreads / 32; ++q) b += red[q];
+    partials[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
   }
 }
 
@@ -146,10 +153,11 @@ cudaError_t launch_stencil_finalize(const Grid& g, double* C, int* flag, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_norm2_partials(const Grid& g, const double* v, double* partials, int* nblocks,
-                                  cudaStream_t st) {
-  dim3 grd((g.H + 31) / 32, (g.Ny + 7) / 8, 2 * g.Nz);
-  k_norm2_partials<<<grd, dim3(32, 8), 0, st>>>(g, v, partials); count_launches(1);
+cudaError_t launch_norm2_partials(const Grid& g, const double* v, double* partials, int cap,
+                                  int* nblocks, cudaStream_t st) {
+  dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
+  if ((int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
+  k_norm2_partials<<<grd, dim3(32, 4), 0, st>>>(g, v, partials); count_launches(1);
   *nblocks = (int)(grd.x * grd.y * grd.z);
   return cudaGetLastError();
 }

@@ -180,21 +180,25 @@ int residual_blocks(const Grid& g) {
 
 template <typename T>
 cudaError_t launch_residual(const Grid& g, const T* C, const T* f, const T* x, T* r,
-                            double* partials, int* nblocks, cudaStream_t st) {
+                            double* partials, int cap, int* nblocks, cudaStream_t st) {
   dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
+  if (partials && (int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
   k_residual<T, 0><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, partials); count_launches(1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
   return cudaGetLastError();
 }
 template cudaError_t launch_residual<double>(const Grid&, const double*, const double*,
-                                             const double*, double*, double*, int*, cudaStream_t);
+                                             const double*, double*, double*, int, int*,
+                                             cudaStream_t);
 template cudaError_t launch_residual<float>(const Grid&, const float*, const float*,
-                                            const float*, float*, double*, int*, cudaStream_t);
+                                            const float*, float*, double*, int, int*,
+                                            cudaStream_t);
 
 cudaError_t launch_residual_mixed(const Grid& g, const double* C, const double* f,
                                   const double* x, float* r32, float* e32, double* partials,
-                                  int* nblocks, cudaStream_t st) {
+                                  int cap, int* nblocks, cudaStream_t st) {
   dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
+  if (partials && (int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
   k_residual<double, 1><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, nullptr, r32, e32, partials); count_launches(1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
   return cudaGetLastError();
