@@ -204,6 +204,28 @@ int mcwind_coarse_solve(mcwind_plan plan, const double* f, double* x, void* stre
  * recursive coarse correction, prolongation and post-smoothing of Sec. 3. */
 int mcwind_vcycle(mcwind_plan plan, int precision, double* x, const double* f, void* stream);
 
+/* Residual norms without allocating anything, for callers that cannot call
+ * cudaMalloc when they check a solution (code running during CUDA graph
+ * capture, where allocation is not capturable; host models whose own pool
+ * owns all device memory).  The paper has no counterpart: this is the
+ * solver's float64 convergence check (Sec. 3 is silent on it) exposed on its
+ * own.  norms (device, 2 doubles) receives ||f_F||_2 and
+ * ||f_F - K_FF lambda_F||_2 with K_FF the plan's assembled finest operator;
+ * f and lambda are device [nz+1][ny+1][nx+1] (entries at fixed nodes are
+ * ignored: lambda counts as 0 there).  Nothing is allocated and the stream is
+ * not synchronized.  The per-block partial sums live in a static device
+ * array of 2 x 131072 doubles (2 MiB, held by every GPU that loads the
+ * library until the process exits): the finest grid may need at most
+ * 131072 blocks of 32 x 4 node columns, i.e. ceil(H/32) * ceil((ny+1)/4) * 2
+ * <= 131072 with H = (nx+2)/2 rounded up to 16; larger plans get
+ * MCWIND_EINVAL before any device work.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current: make that first call before any stream capture.  Every call shares
+ * the array and overwrites what it reads; calls that overlap on the GPU race
+ * on it.  ESTATE if the plan is not assembled. */
+int mcwind_residual_norm_noalloc(mcwind_plan plan, const double* f, const double* lambda,
+                                 double* norms, void* stream);
+
 /* ---- measurement --------------------------------------------------------
  * Kernel classes timed by the optional profiler (CUDA events recorded on the
  * caller's stream around each launch of the class while profiling is on). */

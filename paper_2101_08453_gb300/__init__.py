@@ -91,6 +91,7 @@ def lib():
         "mcwind_level_prolong": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
         "mcwind_coarse_solve": (_i, [_vp, _vp, _vp, _vp]),
         "mcwind_vcycle": (_i, [_vp, _i, _vp, _vp, _vp]),
+        "mcwind_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp]),
         "mcwind_plan_destroy": (None, [_vp]),
         "mcwind_strerror": (ctypes.c_char_p, [_i]),
         "mcwind_last_cuda_error": (_i, []),
@@ -235,6 +236,18 @@ def mcwind_coarse_solve(plan, f, x, stream=None):
 def mcwind_vcycle(plan, precision, x, f, stream=None):
     return _check(lib().mcwind_vcycle(plan, precision, _dev(x, "x"), _dev(f, "f"), _stream(stream)),
                   "mcwind_vcycle")
+
+
+def mcwind_residual_norm_noalloc(plan, f, lam, norms, stream=None):
+    """(||f_F||, ||f_F - K_FF lambda_F||) into the device tensor norms[2],
+    allocating nothing: for callers that cannot call cudaMalloc when they
+    check a solution (during CUDA graph capture, or under a host model that
+    owns all device memory).  Its scratch is a static device array inside
+    the library, shared by all calls: calls that overlap on the GPU race.
+    The first call on a device must come before any stream capture."""
+    return _check(lib().mcwind_residual_norm_noalloc(plan, _dev(f, "f"), _dev(lam, "lambda"),
+                                                     _dev(norms, "norms"), _stream(stream)),
+                  "mcwind_residual_norm_noalloc")
 
 
 class Plan:
