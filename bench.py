@@ -188,7 +188,7 @@ class ClockSampler:
 
 KINDS = ["assemble", "rap", "setup", "rhs", "outer_residual", "smooth_fine", "smooth_coarse",
          "residual_fine", "residual_coarse", "restrict", "prolong", "coarse_solve", "update",
-         "recover", "other"]
+         "recover", "krylov", "other"]
 
 
 def read_profile(m, plan):
@@ -371,22 +371,24 @@ def main():
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp64_peak_tflops = 1.162   # measured FP64 FMA throughput of this GB300 (2 x 5.81e11 FMA/s)
-    g0 = m.lib()
-    dims = plan_dims = (nx + 1, ny + 1, nz + 1)
+    # FP64 pipe: 2 FP64 FMA per clock per SM, measured 5.81e11 FP64 FMA/s on this GB300
+    fp64_peak = 0.581   # T FP64 operations/s (one add, mul or FMA per pipe slot)
+    plan_dims = (nx + 1, ny + 1, nz + 1)
     n_nodes = plan_dims[0] * plan_dims[1] * plan_dims[2]
     n_elem = nx * ny * nz
     csize = 4 if prec == m.PREC_MIXED else 8
-    # algorithmic units of one launch of each class
+    # algorithmic units of one launch of each class (derivations in the design doc)
     algo = {
-        # bytes: 27 coefficients + f + x read + x write per free node of a column group
+        # bytes: 26 off-diagonal coefficients + 1/diagonal + f + x read + x write per free
+        # node of one column group
         "smooth_fine": ("hbm", (27 * csize + 3 * csize) * n_free / 4.0),
         "residual_fine": ("hbm", (27 * csize + 3 * csize) * n_free),
+        # float64 residual: 27 coefficients + f + x + r out (+ float32 r and e out when mixed)
         "outer_residual": ("hbm", (27 * 8 + 3 * 8 + (8 if prec == m.PREC_MIXED else 0)) * n_free),
-        # FP64 flops of one element-class launch: 8 Gauss points x (Jacobian 72, adjugate and
-        # det 21, metric 24, 8 x 9 + 36 x 3 for the element matrix) x 2 flop per FMA
-        "assemble": ("alu", 2.0 * 8 * (72 + 21 + 24 + 72 + 108) * n_elem / 8.0),
-        "rhs": ("alu", 2.0 * 8 * (72 + 21 + 24 + 9 + 24) * n_elem / 8.0),
+        # FP64 operations of one element-parity launch (modal form): stiffness 1700 per
+        # element, load vector 975 per element
+        "assemble": ("alu", 1700.0 * n_elem / 8.0),
+        "rhs": ("alu", 975.0 * n_elem / 8.0),
     }
     dom = max((k for k in prof_main if prof_main[k][1] > 0), key=lambda k: prof_main[k][0])
     roof_kernels = {}
@@ -401,14 +403,15 @@ def main():
                                "frac": ach / hbm_peak, "ms_per_launch": per * 1e3, "launches": n}
         else:
             ach = units / per / 1e12
-            roof_kernels[k] = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops,
-                               "unit": "TFLOP/s", "frac": ach / fp64_peak_tflops,
+            roof_kernels[k] = {"bound": "alu", "achieved": ach, "peak": fp64_peak,
+                               "unit": "T FP64 op/s", "frac": ach / fp64_peak,
                                "ms_per_launch": per * 1e3, "launches": n}
     dom_roof = dict(roof_kernels.get(dom, {"bound": None}))
     dom_roof["kernel"] = dom
     dom_roof["traffic"] = None
-    dom_roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst copy)" if dom_roof.get("bound") == "hbm"
-                               else "measured FP64 FMA rate of this GB300 (1.162 TFLOP/s)")
+    dom_roof["peak_source"] = ("measured: MEASURED_PEAKS.json hbm_gbs (burst copy)"
+                               if dom_roof.get("bound") == "hbm"
+                               else "measured: FP64 FMA issue rate of this GB300, 5.81e11/s")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -69,6 +69,7 @@ enum { MCWIND_RHS_GAUSS8 = 0, MCWIND_RHS_CENTER1 = 1 };
 enum { MCWIND_RULE_PAPER = 0, MCWIND_RULE_OPERATOR = 1 };
 enum { MCWIND_AT_CENTERS = 0, MCWIND_AT_GAUSS = 1 };
 enum { MCWIND_FORWARD = 0, MCWIND_BACKWARD = 1 };
+enum { MCWIND_ACCEL_NONE = 0, MCWIND_ACCEL_CG = 1 };
 
 #define MCWIND_WARM 1u        /* mcwind_solve flag: start from the caller's lambda */
 #define MCWIND_HIST 256
@@ -96,10 +97,16 @@ typedef struct {
      pre-smoothing (column groups 3..0, each column top-down), which makes
      the cycle symmetric; 0: the same order as pre-smoothing. */
   int post_reverse;
+  /* MCWIND_ACCEL_NONE (default): the multigrid iteration of Sec. 3, one
+     V-cycle per iteration.  MCWIND_ACCEL_CG: conjugate gradients with one
+     V-cycle as the preconditioner per iteration (needs post_reverse = 1, the
+     symmetric cycle); same solution, fewer cycles when the cycle alone
+     converges slowly. */
+  int accel;
 } mcwind_options;
 
 typedef struct {
-  int cycles;            /* V-cycles run */
+  int cycles;            /* V-cycles run (one per conjugate-gradient iteration with CG) */
   int status;            /* MCWIND_OK or MCWIND_ENOTCONV */
   double norm_f;         /* ||f_F||_2, f the load vector of Eq. 5 */
   double rel_res;        /* final ||f_F - K_FF lambda_F||_2 / ||f_F||_2 */
@@ -217,7 +224,7 @@ int mcwind_vcycle(mcwind_plan plan, int precision, double* x, const double* f, v
  * array of 2 x 131072 doubles (2 MiB, held by every GPU that loads the
  * library until the process exits): the finest grid may need at most
  * 131072 blocks of 32 x 4 node columns, i.e. ceil(H/32) * ceil((ny+1)/4) * 2
- * <= 131072 with H = (nx+2)/2 rounded up to 16; larger plans get
+ * <= 131072 with H = (nx+2)/2 rounded up to 32; larger plans get
  * MCWIND_EINVAL before any device work.  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current: make that first call before any stream capture.  Every call shares
@@ -244,6 +251,7 @@ enum {
   MCWIND_K_COARSE_SOLVE,    /* dense solve on the coarsest level */
   MCWIND_K_UPDATE,          /* float64 update of the mixed refinement */
   MCWIND_K_RECOVER,         /* u = u0 + A^{-1} grad lambda */
+  MCWIND_K_KRYLOV,          /* conjugate-gradient vector updates and dots */
   MCWIND_K_OTHER,           /* layout conversion, norms, memsets */
   MCWIND_K_KINDS
 };

@@ -28,6 +28,7 @@ RHS_GAUSS8, RHS_CENTER1 = 0, 1
 RULE_PAPER, RULE_OPERATOR = 0, 1
 AT_CENTERS, AT_GAUSS = 0, 1
 FORWARD, BACKWARD = 0, 1
+ACCEL_NONE, ACCEL_CG = 0, 1
 WARM = 1
 HIST = 256
 
@@ -45,7 +46,7 @@ class Options(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("coarsen_rule", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("precision", ctypes.c_int), ("rhs_quad", ctypes.c_int),
-                ("post_reverse", ctypes.c_int)]
+                ("post_reverse", ctypes.c_int), ("accel", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

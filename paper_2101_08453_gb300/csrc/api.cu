@@ -28,43 +28,48 @@ thread_local int g_last_cuda = 0;
 long long launches_now() { return mcwind_launch_count(); }
 
 // Records a CUDA event pair around a kernel class while profiling is on.
+// A scope reserves its two events when it opens; finished pairs are folded
+// into the per-class totals whenever the stream is idle, and the event pool
+// is recycled only when no scope is open.
 struct ProfScope {
   mcwind_plan p;
   int kind;
   cudaStream_t st;
   long long n0 = 0;
+  size_t idx = 0;
   bool on = false;
   ProfScope(mcwind_plan p_, int kind_, cudaStream_t st_) : p(p_), kind(kind_), st(st_) {
     if (!p->prof) return;
-    if (p->ev_used + 2 > p->ev_pool.size()) {
-      for (int q = 0; q < 256; ++q) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return;
-        p->ev_pool.push_back(e);
-      }
+    while (p->ev_used + 2 > p->ev_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      p->ev_pool.push_back(e);
     }
-    if (cudaEventRecord(p->ev_pool[p->ev_used], st) != cudaSuccess) return;
+    idx = p->ev_used;
+    if (cudaEventRecord(p->ev_pool[idx], st) != cudaSuccess) return;
+    p->ev_used += 2;
+    p->prof_open += 1;
     on = true;
     n0 = launches_now();
   }
   ~ProfScope() {
     if (!on) return;
-    cudaEventRecord(p->ev_pool[p->ev_used + 1], st);
-    p->ev_used += 2;
-    p->prof_marks.push_back({kind, (int)(launches_now() - n0)});
+    cudaEventRecord(p->ev_pool[idx + 1], st);
+    p->prof_open -= 1;
+    p->prof_marks.push_back({kind, (int)(launches_now() - n0), idx});
   }
 };
 
-// fold recorded event pairs into the per-class totals (stream must be idle)
+// fold finished event pairs into the per-class totals (stream must be idle)
 void prof_fold(mcwind_plan p) {
-  for (size_t q = 0; q < p->prof_marks.size(); ++q) {
+  for (const auto& mk : p->prof_marks) {
     float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, p->ev_pool[2 * q], p->ev_pool[2 * q + 1]) == cudaSuccess)
-      p->prof_ms[p->prof_marks[q].first] += ms;
-    p->prof_n[p->prof_marks[q].first] += p->prof_marks[q].second;
+    if (cudaEventElapsedTime(&ms, p->ev_pool[mk.idx], p->ev_pool[mk.idx + 1]) == cudaSuccess)
+      p->prof_ms[mk.kind] += ms;
+    p->prof_n[mk.kind] += mk.launches;
   }
   p->prof_marks.clear();
-  p->ev_used = 0;
+  if (p->prof_open == 0) p->ev_used = 0;
 }
 
 #define PROF_CAT2(a, b) a##b
@@ -181,13 +186,16 @@ int outer_residual(mcwind_plan p, cudaStream_t st) {
   Ptr64 A = lv64(p, 0);
   const Grid& g = p->lv[0].g;
   int nb = 0;
-  PROF(MCWIND_K_OUTER_RESIDUAL);
-  if (p->opt.precision == MCWIND_PREC_F64) {
-    CK(launch_residual<double>(g, A.C, A.f, A.x, A.r, partials(p), p->n_partials, &nb, st));
-  } else {
-    Ptr32 B = lv32(p, 0);
-    CK(launch_residual_mixed(g, A.C, A.f, A.x, B.f, B.x, partials(p), p->n_partials, &nb, st));
+  {
+    PROF(MCWIND_K_OUTER_RESIDUAL);
+    if (p->opt.precision == MCWIND_PREC_F64) {
+      CK(launch_residual<double>(g, A.C, A.f, A.x, A.r, partials(p), p->n_partials, &nb, st));
+    } else {
+      Ptr32 B = lv32(p, 0);
+      CK(launch_residual_mixed(g, A.C, A.f, A.x, B.f, B.x, partials(p), p->n_partials, &nb, st));
+    }
   }
+  PROF(MCWIND_K_OTHER);
   CK(launch_reduce_final(partials(p), nb, scal(p) + 1, st));
   return MCWIND_OK;
 }
@@ -321,12 +329,155 @@ extern "C" int mcwind_rhs(mcwind_plan p, const double* u0, double* f, void* stre
   return MCWIND_OK;
 }
 
+namespace {
+
+struct CgVec {
+  double *x, *f, *r, *rp, *p, *q;
+};
+CgVec cg_vectors(mcwind_plan p) {
+  const size_t stride = ((size_t)p->lv[0].g.total * 8 + 255) / 256 * 256;
+  char* b = p->ws + p->off_cg;
+  return {(double*)b, (double*)(b + stride), (double*)(b + 2 * stride), (double*)(b + 3 * stride),
+          (double*)(b + 4 * stride), (double*)(b + 5 * stride)};
+}
+
+// preconditioner input from the current residual (pf = r, px = 0, rp = 0)
+int cg_restart(mcwind_plan p, const CgVec& v, cudaStream_t st) {
+  PROF(MCWIND_K_KRYLOV);
+  const Grid& g = p->lv[0].g;
+  if (p->opt.precision == MCWIND_PREC_F64)
+    CK(launch_cg_start<double>(g, v.r, v.rp, lv64(p, 0).f, lv64(p, 0).x, st));
+  else
+    CK(launch_cg_start<float>(g, v.r, v.rp, lv32(p, 0).f, lv32(p, 0).x, st));
+  return MCWIND_OK;
+}
+
+// r = f - K x (true residual) and ||r||^2 into scal[1]
+int cg_true_residual(mcwind_plan p, const CgVec& v, cudaStream_t st) {
+  const Grid& g = p->lv[0].g;
+  int nb = 0;
+  {
+    PROF(MCWIND_K_OUTER_RESIDUAL);
+    CK(launch_residual<double>(g, lv64(p, 0).C, v.f, v.x, v.r, partials(p), p->n_partials, &nb, st));
+  }
+  PROF(MCWIND_K_OTHER);
+  CK(launch_reduce_final(partials(p), nb, scal(p) + 1, st));
+  return MCWIND_OK;
+}
+
+// one preconditioned CG iteration; ||r||^2 (recursive) into scal[1]
+template <typename T>
+int cg_iteration(mcwind_plan p, const CgVec& v, int first, cudaStream_t st) {
+  CKR(vcycle<T>(p, 0, st));
+  const Grid& g = p->lv[0].g;
+  auto P = Sel<T>::get(p, 0);
+  double* s = scal(p) + 4;
+  {
+    PROF(MCWIND_K_KRYLOV);
+    CK(launch_cg_dots<T>(g, v.r, v.rp, P.x, partials(p), p->n_partials, s, st));
+    CK(launch_cg_direction<T>(g, P.x, v.p, s, first, st));
+  }
+  int nb = 0;
+  {
+    PROF(MCWIND_K_OUTER_RESIDUAL);
+    CK(launch_apply(g, lv64(p, 0).C, v.p, v.q, partials(p), p->n_partials, &nb, st));
+  }
+  {
+    PROF(MCWIND_K_OTHER);
+    CK(launch_reduce_final(partials(p), nb, s + 4, st));
+  }
+  PROF(MCWIND_K_KRYLOV);
+  CK(launch_cg_update<T>(g, v.x, v.r, v.rp, v.p, v.q, P.f, P.x, s, partials(p), p->n_partials,
+                         scal(p) + 1, st));
+  return MCWIND_OK;
+}
+
+int solve_cg(mcwind_plan p, const double* u0, double* lambda, double rtol, int max_cycles,
+             unsigned flags, mcwind_stats& S, cudaStream_t st) {
+  Level& L0 = p->lv[0];
+  const CgVec v = cg_vectors(p);
+  {
+    PROF(MCWIND_K_RHS);
+    CK(cudaMemsetAsync(v.f, 0, sizeof(double) * (size_t)L0.g.total, st));
+    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, p->opt.rhs_quad, v.f, st));
+  }
+  CKR(norm2(p, L0.g, v.f, 0, st));
+  {
+    PROF(MCWIND_K_OTHER);
+    if (flags & MCWIND_WARM)
+      CK(launch_std_to_split<double>(L0.g, lambda, v.x, true, st));
+    else
+      CK(cudaMemsetAsync(v.x, 0, sizeof(double) * (size_t)L0.g.total, st));
+  }
+  CKR(cg_true_residual(p, v, st));
+  double h[2];
+  CKR(read_scalars(p, h, 0, 2, st));
+  const double nf = std::sqrt(h[0]);
+  S.norm_f = nf;
+  if (!std::isfinite(nf) || !std::isfinite(h[1])) return MCWIND_ENONFINITE;
+  int status = MCWIND_OK;
+  if (nf == 0.0) {
+    CK(cudaMemsetAsync(v.x, 0, sizeof(double) * (size_t)L0.g.total, st));
+    S.res_hist[0] = 0.0;
+  } else {
+    S.res_hist[0] = std::sqrt(h[1]) / nf;
+    CKR(cg_restart(p, v, st));
+    int c = 0, first = 1;
+    while (c < max_cycles) {
+      if (S.res_hist[c] <= rtol) {
+        // the recursive residual says converged: confirm with the true one
+        CKR(cg_true_residual(p, v, st));
+        CKR(read_scalars(p, h + 1, 1, 1, st));
+        S.res_hist[c] = std::sqrt(h[1]) / nf;
+        if (S.res_hist[c] <= rtol) break;
+        CKR(cg_restart(p, v, st));
+        first = 1;
+      }
+      if (p->opt.precision == MCWIND_PREC_F64) CKR(cg_iteration<double>(p, v, first, st));
+      else CKR(cg_iteration<float>(p, v, first, st));
+      first = 0;
+      CKR(read_scalars(p, h + 1, 1, 1, st));
+      ++c;
+      S.res_hist[c] = std::sqrt(h[1]) / nf;
+      if (!std::isfinite(S.res_hist[c])) break;
+    }
+    if (c == max_cycles && S.res_hist[c] <= rtol) {
+      CKR(cg_true_residual(p, v, st));
+      CKR(read_scalars(p, h + 1, 1, 1, st));
+      S.res_hist[c] = std::sqrt(h[1]) / nf;
+    }
+    S.cycles = c;
+    if (!(S.res_hist[c] <= rtol)) status = MCWIND_ENOTCONV;
+  }
+  {
+    PROF(MCWIND_K_OTHER);
+    CK(launch_split_to_std<double>(L0.g, v.x, lambda, st));
+  }
+  return status;
+}
+
+}  // namespace
+
 extern "C" int mcwind_solve(mcwind_plan p, const double* u0, double* lambda, double rtol,
                             int max_cycles, unsigned flags, mcwind_stats* stats, void* stream) {
   if (!p || !u0 || !lambda) return MCWIND_EINVAL;
   if (!p->assembled) return MCWIND_ESTATE;
   if (max_cycles < 0 || max_cycles >= MCWIND_HIST || !(rtol >= 0.0)) return MCWIND_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (p->opt.accel == MCWIND_ACCEL_CG) {
+    mcwind_stats S;
+    std::memset(&S, 0, sizeof(S));
+    int status = solve_cg(p, u0, lambda, rtol, max_cycles, flags, S, st);
+    if (status != MCWIND_OK && status != MCWIND_ENOTCONV && status != MCWIND_ENONFINITE) return status;
+    S.rel_res = S.res_hist[S.cycles];
+    if (S.cycles >= 3 && S.res_hist[2] > 0.0)
+      S.rate = std::pow(S.res_hist[S.cycles] / S.res_hist[2], 1.0 / (S.cycles - 2));
+    else if (S.cycles >= 1 && S.res_hist[0] > 0.0)
+      S.rate = std::pow(S.res_hist[S.cycles] / S.res_hist[0], 1.0 / S.cycles);
+    S.status = status;
+    if (stats) *stats = S;
+    return status;
+  }
   Level& L0 = p->lv[0];
   Ptr64 A = lv64(p, 0);
   // load vector f (Eq. 5 right side) and its norm

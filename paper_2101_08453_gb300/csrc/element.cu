@@ -8,6 +8,18 @@
 // With adj = det(J) J^{-1}:
 //   detJ grad N_m . A^{-1} grad N_n = dN_m^T (adj D adj^T / detJ) dN_n,
 //   detJ grad N_m . v               = dN_m^T (adj v),       D = diag(a^-2).
+// The 2x2x2 Gauss sums are taken in the modal (Walsh) basis of the trilinear
+// space: with phi_S = prod_{b in S} xi_b (S a subset of {0,1,2}) the shape
+// functions are N_n = 1/8 sum_S eps_n^S phi_S, eps_n^S = prod_{b in S} eps_{n,b},
+// so with the Gauss-point sign sums  C^_q = sum_g sigma_q(g) C_g
+// (sigma_q(g) = prod_{b in q} sign(xi_{g,b}), xi_g = +-1/sqrt(3) =: +-s):
+//   K^[S][T] = s^(|S|+|T|-2) sum_{a in S, b in T} C^_{(S) xor (T)}[a][b],
+//   K_e      = 1/64 H K^ H^T,   H[n][S] = eps_n^S = (-1)^|S| W[n][S],
+// W the 8-point Walsh-Hadamard matrix: two fast transforms instead of the
+// 8 x 36 three-term products of the nodal form.  The load vector is done the
+// same way with w_g = adj(J_g) u0(g).  Every Gauss loop is unrolled, so the
+// shape-function values are compile-time constants.
+//
 // Assembly scatters element contributions in 8 launches, one per element
 // parity class (i mod 2, j mod 2, k mod 2): elements of one class share no
 // node, so there are no atomics and the sums are deterministic.
@@ -116,6 +128,34 @@ __device__ __forceinline__ bool elem_of_thread(int nx, int ny, int nz, int cls, 
   return i < nx && j < ny && k < nz;
 }
 
+// sigma_q(g): product over the bits b of q of (+1 if bit b of g is set, else -1)
+__host__ __device__ constexpr double sgn(int q, int g) {
+  return ((q & 1) && !(g & 1) ? -1.0 : 1.0) * ((q & 2) && !(g & 2) ? -1.0 : 1.0) *
+         ((q & 4) && !(g & 4) ? -1.0 : 1.0);
+}
+__host__ __device__ constexpr int popc3(int q) { return (q & 1) + ((q >> 1) & 1) + ((q >> 2) & 1); }
+// index of the symmetric 3x3 component (a, b) in (00, 01, 02, 11, 12, 22)
+__host__ __device__ constexpr int sym6(int a, int b) {
+  return (a < b ? a : b) == 0 ? (a < b ? b : a) : ((a < b ? a : b) == 1 ? 2 + (a < b ? b : a) : 5);
+}
+__host__ __device__ constexpr double spow(int e) {
+  return e == 0 ? 1.0 : (e == 1 ? kGp : (e == 2 ? kGp * kGp : (e == 3 ? kGp * kGp * kGp : kGp * kGp * kGp * kGp)));
+}
+
+// in-place 8-point Walsh-Hadamard transform y[n] = sum_S (-1)^popcount(n & S) x[S]
+__device__ __forceinline__ void wht8(double x[8]) {
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; i += 2 * h)
+#pragma unroll
+      for (int j = i; j < i + h; ++j) {
+        const double a = x[j], b = x[j + h];
+        x[j] = a + b;
+        x[j + h] = a - b;
+      }
+}
+
 __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny, int nz,
                                                           const double* __restrict__ X,
                                                           const double* __restrict__ Y,
@@ -127,46 +167,78 @@ __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny
   if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
   Geo G;
   load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
-  double Ke[8][8];
+  double Ch[8][6];
 #pragma unroll
-  for (int m = 0; m < 8; ++m)
+  for (int q = 0; q < 8; ++q)
 #pragma unroll
-    for (int n = 0; n < 8; ++n) Ke[m][n] = 0.0;
+    for (int c = 0; c < 6; ++c) Ch[q][c] = 0.0;
   bool bad = false;
-#pragma unroll 1
+#pragma unroll
   for (int gp = 0; gp < 8; ++gp) {
     double xi[3], J[3][3], adj[3][3];
     gauss_xi(gp, xi);
     jacobian_at(G, xi, J);
-    double det = adjugate(J, adj);
+    const double det = adjugate(J, adj);
     bad |= !(det > 0.0);
-    double inv = 1.0 / det;
-    // Cm = adj D adj^T / det (symmetric)
-    double Cm[3][3];
+    const double inv = 1.0 / det;
+    double aD[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      aD[r][0] = adj[r][0] * d0;
+      aD[r][1] = adj[r][1] * d1;
+      aD[r][2] = adj[r][2] * d2;
+    }
+    double c6[6];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int t = r; t < 3; ++t) {
-        double s = adj[r][0] * adj[t][0] * d0 + adj[r][1] * adj[t][1] * d1 +
-                   adj[r][2] * adj[t][2] * d2;
-        Cm[r][t] = s * inv;
-        Cm[t][r] = s * inv;
-      }
-    double dN[8][3], v[8][3];
+      for (int t = r; t < 3; ++t)
+        c6[sym6(r, t)] = (aD[r][0] * adj[t][0] + aD[r][1] * adj[t][1] + aD[r][2] * adj[t][2]) * inv;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      dshape(n, xi, dN[n]);
+    for (int q = 0; q < 8; ++q)
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-        v[n][r] = Cm[r][0] * dN[n][0] + Cm[r][1] * dN[n][1] + Cm[r][2] * dN[n][2];
-    }
-#pragma unroll
-    for (int m = 0; m < 8; ++m)
-#pragma unroll
-      for (int n = m; n < 8; ++n)
-        Ke[m][n] += dN[m][0] * v[n][0] + dN[m][1] * v[n][1] + dN[m][2] * v[n][2];
+      for (int c = 0; c < 6; ++c) Ch[q][c] += sgn(q, gp) * c6[c];
   }
   if (bad) atomicOr(flag, 1);
+  // K~ = D K^ D / 64 (D[S] = (-1)^|S|); row and column 0 vanish
+  double Kt[8][8];
+#pragma unroll
+  for (int S = 0; S < 8; ++S)
+#pragma unroll
+    for (int T = 0; T < 8; ++T) {
+      if (S == 0 || T == 0 || T < S) continue;
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (!((S >> a) & 1)) continue;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if (!((T >> b) & 1)) continue;
+          v += Ch[(S & ~(1 << a)) ^ (T & ~(1 << b))][sym6(a, b)];
+        }
+      }
+      const int e = popc3(S) + popc3(T);
+      Kt[S][T] = v * (spow(e - 2) * ((e & 1) ? -1.0 : 1.0) / 64.0);
+    }
+#pragma unroll
+  for (int S = 0; S < 8; ++S)
+#pragma unroll
+    for (int T = 0; T < 8; ++T) {
+      if (S == 0 || T == 0) Kt[S][T] = 0.0;
+      else if (T < S) Kt[S][T] = Kt[T][S];
+    }
+  // K_e = W K~ W: transform the rows, then the columns
+#pragma unroll
+  for (int S = 1; S < 8; ++S) wht8(Kt[S]);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    double col[8];
+#pragma unroll
+    for (int S = 0; S < 8; ++S) col[S] = Kt[S][n];
+    wht8(col);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) Kt[m][n] = col[m];
+  }
   // scatter: row of local node m gets Ke[m][n] at offset (n - m)
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -179,37 +251,59 @@ __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny
       if (!is_free(g, in, jn, kn)) continue;
       int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
               9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-      double val = (n >= m) ? Ke[m][n] : Ke[n][m];
-      C[(int64_t)s * g.total + row] += val;
+      C[(int64_t)s * g.total + row] += (n >= m) ? Kt[m][n] : Kt[n][m];
     }
   }
 }
 
-// sum_g dN_m(g) . (adj(J_g) v_g) for the 8 local nodes; v_g supplied by Vsrc.
+// out[m] = sum_g dN_m(g) . (adj(J_g) v_g) for the 8 local nodes (v_g supplied by
+// Vsrc): with w^_q = sum_g sigma_q(g) w_g the modal load is
+// f^[S] = s^(|S|-1) sum_{a in S} w^_{S\a}[a] and out = 1/8 H f^.
+// quad 1 is the one-point rule at the center (weight 8): out[m] = eps_m . (adj(J_0) v_0).
 template <typename Vsrc>
 __device__ __forceinline__ void weak_div_elem(const Geo& G, int quad, const Vsrc& vsrc,
                                               double out[8]) {
+  if (quad != 0) {
+    double xi[3] = {0.0, 0.0, 0.0}, J[3][3], adj[3][3], v[3], w[3];
+    jacobian_at(G, xi, J);
+    adjugate(J, adj);
+    vsrc(0, xi, v);
 #pragma unroll
-  for (int m = 0; m < 8; ++m) out[m] = 0.0;
-  const int ng = quad == 0 ? 8 : 1;
-#pragma unroll 1
-  for (int gp = 0; gp < ng; ++gp) {
-    double xi[3] = {0.0, 0.0, 0.0}, J[3][3], adj[3][3], v[3];
-    double wgt = 8.0;
-    if (quad == 0) { gauss_xi(gp, xi); wgt = 1.0; }
+    for (int r = 0; r < 3; ++r) w[r] = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+      out[m] = ((m & 1) ? w[0] : -w[0]) + ((m & 2) ? w[1] : -w[1]) + ((m & 4) ? w[2] : -w[2]);
+    return;
+  }
+  double wh[8][3];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) wh[q][0] = wh[q][1] = wh[q][2] = 0.0;
+#pragma unroll
+  for (int gp = 0; gp < 8; ++gp) {
+    double xi[3], J[3][3], adj[3][3], v[3];
+    gauss_xi(gp, xi);
     jacobian_at(G, xi, J);
     adjugate(J, adj);
     vsrc(gp, xi, v);
     double w[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) w[r] = wgt * (adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2]);
+    for (int r = 0; r < 3; ++r) w[r] = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      double dN[3];
-      dshape(m, xi, dN);
-      out[m] += dN[0] * w[0] + dN[1] * w[1] + dN[2] * w[2];
-    }
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) wh[q][r] += sgn(q, gp) * w[r];
   }
+  // f~[S] = (-1)^|S| f^[S] / 8, then out = W f~
+#pragma unroll
+  for (int S = 0; S < 8; ++S) {
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if ((S >> a) & 1) v += wh[S & ~(1 << a)][a];
+    const int e = popc3(S);
+    out[S] = S == 0 ? 0.0 : v * (spow(e - 1) * ((e & 1) ? -1.0 : 1.0) * 0.125);
+  }
+  wht8(out);
 }
 
 struct NodalInterp {
@@ -287,13 +381,14 @@ __global__ void __launch_bounds__(128) k_weak_div(int nx, int ny, int nz,
     out[sidx(nx + 1, ny + 1, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] += be[m];
 }
 
+template <int NG>
 __global__ void __launch_bounds__(128) k_recover(Grid g, int nx, int ny, int nz,
                                                  const double* __restrict__ X,
                                                  const double* __restrict__ Y,
                                                  const double* __restrict__ Z,
                                                  const double* __restrict__ u0,
                                                  const double* __restrict__ lam, double d0,
-                                                 double d1, double d2, int where,
+                                                 double d1, double d2,
                                                  double* __restrict__ u) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -307,12 +402,12 @@ __global__ void __launch_bounds__(128) k_recover(Grid g, int nx, int ny, int nz,
 #pragma unroll
   for (int n = 0; n < 8; ++n) le[n] = lam[gidx(g, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1))];
   int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
-  const int ng = where == 0 ? 1 : 8;
+  const int ng = NG;
   const double dd[3] = {d0, d1, d2};
-#pragma unroll 1
-  for (int gp = 0; gp < ng; ++gp) {
+#pragma unroll
+  for (int gp = 0; gp < NG; ++gp) {
     double xi[3] = {0.0, 0.0, 0.0}, J[3][3], adj[3][3];
-    if (where != 0) gauss_xi(gp, xi);
+    if (NG == 8) gauss_xi(gp, xi);
     jacobian_at(G, xi, J);
     double det = adjugate(J, adj);
     double gr[3] = {0.0, 0.0, 0.0}, up[3] = {0.0, 0.0, 0.0};
@@ -386,8 +481,13 @@ cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* 
                            cudaStream_t st) {
   dim3 blk(32, 4, 1);
   dim3 grd((nx + 31) / 32, (ny + 3) / 4, nz);
-  k_recover<<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, lam, 1.0 / (a[0] * a[0]),
-                                 1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), where, u); count_launches(1);
+  if (where == 0)
+    k_recover<1><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, lam, 1.0 / (a[0] * a[0]),
+                                      1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u);
+  else
+    k_recover<8><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, lam, 1.0 / (a[0] * a[0]),
+                                      1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -8,10 +8,14 @@
 // warp over consecutive same-group columns reads the stencil planes with
 // unit stride instead of stride 2.
 //
-// A level's operator is stored as 28 planes of that layout: plane
+// A level's float64 operator is stored as 28 planes of that layout: plane
 // s = (di+1) + 3(dj+1) + 9(dk+1) (s = 13 the diagonal) holds K_FF(n, n+d),
 // plane 27 holds 1/K(n, n).  Rows and columns of fixed (Dirichlet) nodes
 // are zero, so the planes hold exactly the free block K_FF of Eq. 5.
+// The float32 copy is tiled instead: the 28 coefficients of 32 consecutive
+// nodes of a half row are one contiguous 3584-byte tile (coefficient s of
+// node b at ((b >> 5) * 28 + s) * 32 + (b & 31)), so a warp stepping
+// through a layer reads one contiguous block rather than 28 planes.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,7 +37,7 @@ void count_launches(int n);
 
 struct Grid {
   int Nx, Ny, Nz;
-  int H;          // half-row pitch (elements)
+  int H;          // half-row pitch (elements, a multiple of 32)
   int64_t RP;     // row pitch = 2H
   int64_t PP;     // layer pitch = Ny*RP
   int64_t total;  // Nz*PP
@@ -43,7 +47,7 @@ inline Grid make_grid(int Nx, int Ny, int Nz) {
   Grid g;
   g.Nx = Nx; g.Ny = Ny; g.Nz = Nz;
   int half = (Nx + 1) / 2;
-  g.H = (half + 15) / 16 * 16;
+  g.H = (half + 31) / 32 * 32;
   g.RP = 2 * (int64_t)g.H;
   g.PP = (int64_t)Ny * g.RP;
   g.total = (int64_t)Nz * g.PP;
@@ -52,6 +56,14 @@ inline Grid make_grid(int Nx, int Ny, int Nz) {
 
 __host__ __device__ inline int64_t gidx(const Grid& g, int i, int j, int k) {
   return (int64_t)k * g.PP + (int64_t)j * g.RP + (int64_t)(i & 1) * g.H + (i >> 1);
+}
+
+// coefficient s of node b (split-layout index): planar float64, tiled float32
+__device__ __forceinline__ double coef(const double* C, int64_t total, int64_t b, int s) {
+  return C[(int64_t)s * total + b];
+}
+__device__ __forceinline__ float coef(const float* C, int64_t, int64_t b, int s) {
+  return C[((b >> 5) * kPlanes + s) * 32 + (b & 31)];
 }
 
 __host__ __device__ inline bool is_free(const Grid& g, int i, int j, int k) {
@@ -69,27 +81,29 @@ struct Transfer {
   int Nzf, Nzc;
   int kf[kMaxZ];             // coarse K -> fine k
   int kc0[kMaxZ], kc1[kMaxZ];  // fine k -> coarse layers (kc1 = kc0 when one)
-  double kw0[kMaxZ], kw1[kMaxZ];
+  float kw0[kMaxZ], kw1[kMaxZ];  // their weights (0, 1/2 or 1: exact in float)
 };
 
-// 1-D interpolation pair of a horizontal fine index f (Nf fine, Nc coarse nodes).
-__host__ __device__ inline void hpair(int coarsen, int Nf, int Nc, int f, int& c0, double& w0,
-                                      int& c1, double& w1) {
-  if (!coarsen) { c0 = c1 = f; w0 = 1.0; w1 = 0.0; return; }
-  if (f == Nf - 1) { c0 = c1 = Nc - 1; w0 = 1.0; w1 = 0.0; return; }
-  if ((f & 1) == 0) { c0 = c1 = f >> 1; w0 = 1.0; w1 = 0.0; return; }
-  c0 = (f - 1) >> 1; c1 = (f + 1) >> 1; w0 = 0.5; w1 = 0.5;
+// 1-D interpolation pair of a horizontal fine index f (Nf fine, Nc coarse
+// nodes); the weights (0, 1/2, 1) are exact in any floating type W.
+template <typename W>
+__host__ __device__ inline void hpair(int coarsen, int Nf, int Nc, int f, int& c0, W& w0, int& c1,
+                                      W& w1) {
+  if (!coarsen) { c0 = c1 = f; w0 = W(1); w1 = W(0); return; }
+  if (f == Nf - 1) { c0 = c1 = Nc - 1; w0 = W(1); w1 = W(0); return; }
+  if ((f & 1) == 0) { c0 = c1 = f >> 1; w0 = W(1); w1 = W(0); return; }
+  c0 = (f - 1) >> 1; c1 = (f + 1) >> 1; w0 = W(0.5); w1 = W(0.5);
   if (f + 1 == Nf - 1) c1 = Nc - 1;
 }
 
 // Fine node of horizontal coarse index I and the weights of its fine
 // neighbours f-1 and f+1 in the restriction.
-__host__ __device__ inline void hcoarse(int coarsen, int Nf, int Nc, int I, int& f, double& wm,
-                                        double& wp) {
-  if (!coarsen) { f = I; wm = wp = 0.0; return; }
+template <typename W>
+__host__ __device__ inline void hcoarse(int coarsen, int Nf, int Nc, int I, int& f, W& wm, W& wp) {
+  if (!coarsen) { f = I; wm = wp = W(0); return; }
   f = (I == Nc - 1) ? Nf - 1 : 2 * I;
-  wm = (f >= 1 && ((f - 1) & 1)) ? 0.5 : 0.0;
-  wp = (f + 1 <= Nf - 2 && ((f + 1) & 1)) ? 0.5 : 0.0;
+  wm = (f >= 1 && ((f - 1) & 1)) ? W(0.5) : W(0);
+  wp = (f + 1 <= Nf - 2 && ((f + 1) & 1)) ? W(0.5) : W(0);
 }
 
 struct Level {
@@ -120,6 +134,7 @@ struct mcwind_plan_s {
   size_t off_partials = 0;                  // reduction partials
   size_t off_scalars = 0;                   // device scalars / flags
   size_t off_cfree = 0;                     // coarsest free-node grid indices
+  size_t off_cg = 0;                        // 6 finest-level float64 vectors of CG
   int n_coarse = 0;
   int n_partials = 0;
   // bound at assemble
@@ -130,7 +145,13 @@ struct mcwind_plan_s {
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  std::vector<std::pair<int, int>> prof_marks;  // (kind, launches) per event pair
+  struct ProfMark {
+    int kind;
+    int launches;
+    size_t idx;  // start event; idx + 1 is the end event
+  };
+  std::vector<ProfMark> prof_marks;
+  int prof_open = 0;
   double prof_ms[MCWIND_K_KINDS] = {0};
   long long prof_n[MCWIND_K_KINDS] = {0};
   // per-plan CUDA objects

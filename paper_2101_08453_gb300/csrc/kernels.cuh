@@ -58,6 +58,9 @@ cudaError_t launch_residual(const Grid& g, const T* C, const T* f, const T* x, T
 cudaError_t launch_residual_mixed(const Grid& g, const double* C, const double* f,
                                   const double* x, float* r32, float* e32, double* partials,
                                   int cap, int* nblocks, cudaStream_t st);
+// y = K x at free nodes (0 elsewhere), partials of x . K x (float64)
+cudaError_t launch_apply(const Grid& g, const double* C, const double* x, double* y,
+                         double* partials, int cap, int* nblocks, cudaStream_t st);
 // x64 += e32 at free nodes
 cudaError_t launch_update_mixed(const Grid& g, double* x, const float* e, cudaStream_t st);
 template <typename T>
@@ -82,5 +85,24 @@ cudaError_t launch_dense_invert(double* A, double* B, int n, double** result, cu
 template <typename T>
 cudaError_t launch_dense_solve(const double* Ainv, int n, const int* cfree, const T* f, T* x,
                                cudaStream_t st);
+
+// ---- krylov.cu: V-cycle-preconditioned conjugate gradients ----
+// device scalars s[0..4] = (r.z, r_prev.z, previous r.z, beta, p.Kp)
+int krylov_blocks(const Grid& g);
+template <typename TZ>
+cudaError_t launch_cg_dots(const Grid& g, const double* r, const double* rp, const TZ* z,
+                           double* partials, int cap, double* s, cudaStream_t st);
+template <typename TZ>
+cudaError_t launch_cg_direction(const Grid& g, const TZ* z, double* p, double* s, int first,
+                                cudaStream_t st);
+template <typename TP>
+cudaError_t launch_cg_update(const Grid& g, double* x, double* r, double* rp, const double* p,
+                             const double* q, TP* pf, TP* px, double* s, double* partials,
+                             int cap, double* rr_out, cudaStream_t st);
+template <typename TP>
+cudaError_t launch_cg_start(const Grid& g, const double* r, double* rp, TP* pf, TP* px,
+                            cudaStream_t st);
+cudaError_t launch_reduce_pairs(const double* partials, int n, double* out0, double* out1,
+                                cudaStream_t st);
 
 }  // namespace mcw

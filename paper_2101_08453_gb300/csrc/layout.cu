@@ -44,13 +44,18 @@ __global__ void k_stencil_export(Grid g, const T* __restrict__ C, double* __rest
   int64_t o = ((int64_t)k * g.Ny + j) * g.Nx + i;
   int64_t id = gidx(g, i, j, k);
 #pragma unroll
-  for (int s = 0; s < 27; ++s) out[s * n + o] = (double)C[s * g.total + id];
+  for (int s = 0; s < 27; ++s) out[s * n + o] = (double)coef(C, g.total, id, s);
 }
 
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t st = (int64_t)gridDim.x * blockDim.x;
-  for (; i < n; i += st) b[i] = (float)a[i];
+// planar float64 operator -> tiled float32 copy (one thread per node index b)
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ t, int64_t total) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; b < total; b += st) {
+    float* dst = t + (b >> 5) * (kPlanes * 32) + (b & 31);
+#pragma unroll 4
+    for (int s = 0; s < kPlanes; ++s) dst[s * 32] = (float)a[(int64_t)s * total + b];
+  }
 }
 
 __global__ void k_finalize(Grid g, double* __restrict__ C, int* flag) {
@@ -142,9 +147,8 @@ template cudaError_t launch_stencil_export<double>(const Grid&, const double*, d
 template cudaError_t launch_stencil_export<float>(const Grid&, const float*, double*, cudaStream_t);
 
 cudaError_t launch_stencil_to_f32(const Grid& g, const double* C64, float* C32, cudaStream_t st) {
-  int64_t n = (int64_t)kPlanes * g.total;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  k_to_f32<<<blocks, 256, 0, st>>>(C64, C32, n); count_launches(1);
+  int blocks = (int)std::min<int64_t>((g.total + 255) / 256, 152 * 16);
+  k_to_f32<<<blocks, 256, 0, st>>>(C64, C32, g.total); count_launches(1);
   return cudaGetLastError();
 }
 

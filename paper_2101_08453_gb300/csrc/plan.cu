@@ -78,12 +78,12 @@ static Transfer make_transfer(int hx, int hy, int Nzf, const std::vector<int>& k
   Transfer t;
   t.hx = hx; t.hy = hy; t.Nzf = Nzf; t.Nzc = (int)kmap.size();
   for (int K = 0; K < kMaxZ; ++K) t.kf[K] = K < t.Nzc ? kmap[K] : 0;
-  for (int k = 0; k < kMaxZ; ++k) { t.kc0[k] = t.kc1[k] = 0; t.kw0[k] = t.kw1[k] = 0.0; }
+  for (int k = 0; k < kMaxZ; ++k) { t.kc0[k] = t.kc1[k] = 0; t.kw0[k] = t.kw1[k] = 0.0f; }
   for (int K = 0; K < t.Nzc; ++K) {
     const int k = kmap[K];
-    t.kc0[k] = t.kc1[k] = K; t.kw0[k] = 1.0; t.kw1[k] = 0.0;
+    t.kc0[k] = t.kc1[k] = K; t.kw0[k] = 1.0f; t.kw1[k] = 0.0f;
     if (K + 1 < t.Nzc && kmap[K + 1] - k == 2) {
-      t.kc0[k + 1] = K; t.kc1[k + 1] = K + 1; t.kw0[k + 1] = 0.5; t.kw1[k + 1] = 0.5;
+      t.kc0[k + 1] = K; t.kc1[k + 1] = K + 1; t.kw0[k + 1] = 0.5f; t.kw1[k + 1] = 0.5f;
     }
   }
   return t;
@@ -104,6 +104,7 @@ extern "C" void mcwind_default_options(mcwind_options* o) {
   o->precision = MCWIND_PREC_F64;
   o->rhs_quad = MCWIND_RHS_GAUSS8;
   o->post_reverse = 1;
+  o->accel = MCWIND_ACCEL_NONE;
 }
 
 extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], double h1,
@@ -131,6 +132,8 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   if (o.precision != MCWIND_PREC_F64 && o.precision != MCWIND_PREC_MIXED) return MCWIND_EINVAL;
   if (o.rhs_quad != MCWIND_RHS_GAUSS8 && o.rhs_quad != MCWIND_RHS_CENTER1) return MCWIND_EINVAL;
   if (o.post_reverse != 0 && o.post_reverse != 1) return MCWIND_EINVAL;
+  if (o.accel != MCWIND_ACCEL_NONE && o.accel != MCWIND_ACCEL_CG) return MCWIND_EINVAL;
+  if (o.accel == MCWIND_ACCEL_CG && o.post_reverse != 1) return MCWIND_EINVAL;
 
   std::vector<PlanLevel> H = hierarchy(nx, ny, nz, a, h1, h3, o.coarsen_rule, o.coarsest_max);
   if (H.empty() || !H.back().kmap.empty()) return MCWIND_EINVAL;
@@ -185,8 +188,13 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   p->n_coarse = (int)nc;
   p->off_dense = off; off = align256(off + 2 * (size_t)nc * nc * 8);
   p->off_cfree = off; off = align256(off + (size_t)nc * 4);
-  p->n_partials = max_blocks;
-  p->off_partials = off; off = align256(off + (size_t)max_blocks * 8);
+  if (o.accel == MCWIND_ACCEL_CG) {
+    const size_t t0 = (size_t)p->lv[0].g.total;
+    p->off_cg = off;
+    off = align256(off + 6 * align256(t0 * 8));
+  }
+  p->n_partials = 2 * max_blocks;
+  p->off_partials = off; off = align256(off + (size_t)p->n_partials * 8);
   p->off_scalars = off; off = align256(off + 256);
   p->ws_bytes = off;
   *out = p;

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128) k_rap(Grid gin, Grid gout, Transfer tr,
       if (DIM < 2) {
         hpair(1, Nf, Nc, b, c0, w0, c1, w1);
       } else {
-        c0 = tr.kc0[b]; c1 = tr.kc1[b]; w0 = tr.kw0[b]; w1 = tr.kw1[b];
+        c0 = tr.kc0[b]; c1 = tr.kc1[b]; w0 = (double)tr.kw0[b]; w1 = (double)tr.kw1[b];
       }
     }
 #pragma unroll

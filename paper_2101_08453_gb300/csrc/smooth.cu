@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(128) k_gs(Grid g, const T* __restrict__ C,
       T acc = f[b];
 #pragma unroll
       for (int s = 0; s < 27; ++s)
-        if (s != kDiag) acc -= C[s * tot + b] * w[s / 9][s % 9];
-      const T xn = acc * C[kInvDiag * tot + b];
+        if (s != kDiag) acc -= coef(C, tot, b, s) * w[s / 9][s % 9];
+      const T xn = acc * coef(C, tot, b, kInvDiag);
       x[b] = xn;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(128) k_gs(Grid g, const T* __restrict__ C,
       T acc = f[b];
 #pragma unroll
       for (int s = 0; s < 27; ++s)
-        if (s != kDiag) acc -= C[s * tot + b] * w[s / 9][s % 9];
-      const T xn = acc * C[kInvDiag * tot + b];
+        if (s != kDiag) acc -= coef(C, tot, b, s) * w[s / 9][s % 9];
+      const T xn = acc * coef(C, tot, b, kInvDiag);
       x[b] = xn;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {

@@ -24,7 +24,8 @@ __device__ __forceinline__ void block_partial(double s, double* partials) {
 
 // r = f - K x over one column, all k, both parities (blockIdx.z = parity).
 // MODE 0: write r (type T).  MODE 1 (T = double): write (float) r into r32
-// and zero e32, the start of one float32 correction cycle.
+// and zero e32, the start of one float32 correction cycle.  MODE 2: r = K x
+// (f unused) and the partials of x . K x instead of r . r.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __restrict__ C,
                                                           const T* __restrict__ f,
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __res
     if (!fcol) {
       for (int k = 0; k < g.Nz; ++k) {
         const int64_t b = (int64_t)k * PP + own;
-        if (MODE == 0) r[b] = T(0);
+        if (MODE != 1) r[b] = T(0);
         else { r32[b] = 0.0f; e32[b] = 0.0f; }
       }
     } else {
@@ -63,11 +64,19 @@ __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __res
       }
       for (int k = 0; k <= g.Nz - 2; ++k) {
         const int64_t b = (int64_t)k * PP + own;
-        T acc = f[b];
+        T acc;
+        if (MODE == 2) {
+          acc = T(0);
 #pragma unroll
-        for (int s = 0; s < 27; ++s) acc -= C[s * tot + b] * w[s / 9][s % 9];
-        ss += (double)acc * (double)acc;
-        if (MODE == 0) r[b] = acc;
+          for (int s = 0; s < 27; ++s) acc += coef(C, tot, b, s) * w[s / 9][s % 9];
+          ss += (double)acc * (double)w[1][4];
+        } else {
+          acc = f[b];
+#pragma unroll
+          for (int s = 0; s < 27; ++s) acc -= coef(C, tot, b, s) * w[s / 9][s % 9];
+          ss += (double)acc * (double)acc;
+        }
+        if (MODE != 1) r[b] = acc;
         else { r32[b] = (float)acc; e32[b] = 0.0f; }
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
@@ -83,7 +92,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __res
         }
       }
       const int64_t b = (int64_t)(g.Nz - 1) * PP + own;
-      if (MODE == 0) r[b] = T(0);
+      if (MODE != 1) r[b] = T(0);
       else { r32[b] = 0.0f; e32[b] = 0.0f; }
     }
   }
@@ -108,12 +117,16 @@ __global__ void k_update_mixed(Grid g, double* __restrict__ x, const float* __re
 }
 
 // vertical restriction weights of coarse layer K
-__device__ __forceinline__ void vcoarse(const Transfer& tr, int K, int& f, double& wm, double& wp) {
+template <typename W>
+__device__ __forceinline__ void vcoarse(const Transfer& tr, int K, int& f, W& wm, W& wp) {
   f = tr.kf[K];
-  wm = (K > 0 && tr.kf[K] - tr.kf[K - 1] == 2) ? 0.5 : 0.0;
-  wp = (K < tr.Nzc - 1 && tr.kf[K + 1] - tr.kf[K] == 2) ? 0.5 : 0.0;
+  wm = (K > 0 && tr.kf[K] - tr.kf[K - 1] == 2) ? W(0.5) : W(0);
+  wp = (K < tr.Nzc - 1 && tr.kf[K + 1] - tr.kf[K] == 2) ? W(0.5) : W(0);
 }
 
+// f_c = P^T r at one coarse node: up to 3 x 3 x 3 fine residuals with the
+// interpolation weights (1 at the coarse node, 1/2 at the half nodes around
+// it), accumulated in the precision of the cycle (T).
 template <typename T>
 __global__ void k_restrict(Grid gf, Grid gc, Transfer tr, const T* __restrict__ r,
                            T* __restrict__ fc) {
@@ -122,54 +135,59 @@ __global__ void k_restrict(Grid gf, Grid gc, Transfer tr, const T* __restrict__ 
   const int64_t out = gidx(gc, I, J, K);
   if (!is_free(gc, I, J, K)) { fc[out] = T(0); return; }
   int fi, fj, fk;
-  double wx[3], wy[3], wz[3];
-  hcoarse(tr.hx, gf.Nx, gc.Nx, I, fi, wx[0], wx[2]);
-  hcoarse(tr.hy, gf.Ny, gc.Ny, J, fj, wy[0], wy[2]);
-  vcoarse(tr, K, fk, wz[0], wz[2]);
-  wx[1] = wy[1] = wz[1] = 1.0;
-  double s = 0.0;
+  T ax[3], ay[3], az[3];
+  hcoarse(tr.hx, gf.Nx, gc.Nx, I, fi, ax[0], ax[2]);
+  hcoarse(tr.hy, gf.Ny, gc.Ny, J, fj, ay[0], ay[2]);
+  vcoarse(tr, K, fk, az[0], az[2]);
+  ax[1] = ay[1] = az[1] = T(1);
+  T s = T(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    if (wz[c] == 0.0) continue;
+    if (az[c] == T(0)) continue;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      if (wy[b] == 0.0) continue;
+      if (ay[b] == T(0)) continue;
+      T row = T(0);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        if (wx[a] == 0.0) continue;
-        s += wx[a] * wy[b] * wz[c] * (double)r[gidx(gf, fi + a - 1, fj + b - 1, fk + c - 1)];
+        if (ax[a] == T(0)) continue;
+        row += ax[a] * r[gidx(gf, fi + a - 1, fj + b - 1, fk + c - 1)];
       }
+      s += (ay[b] * az[c]) * row;
     }
   }
-  fc[out] = (T)s;
+  fc[out] = s;
 }
 
+// x += P e_c at one fine node: up to 2 x 2 x 2 coarse values, in precision T.
 template <typename T>
 __global__ void k_prolong_add(Grid gf, Grid gc, Transfer tr, const T* __restrict__ ec,
                               T* __restrict__ x) {
   int i, j, k;
   if (!node_of_thread(gf, i, j, k) || !is_free(gf, i, j, k)) return;
   int ci[2], cj[2], ck[2];
-  double wx[2], wy[2], wz[2];
-  hpair(tr.hx, gf.Nx, gc.Nx, i, ci[0], wx[0], ci[1], wx[1]);
-  hpair(tr.hy, gf.Ny, gc.Ny, j, cj[0], wy[0], cj[1], wy[1]);
-  ck[0] = tr.kc0[k]; ck[1] = tr.kc1[k]; wz[0] = tr.kw0[k]; wz[1] = tr.kw1[k];
-  double s = 0.0;
+  T ax[2], ay[2], az[2];
+  hpair(tr.hx, gf.Nx, gc.Nx, i, ci[0], ax[0], ci[1], ax[1]);
+  hpair(tr.hy, gf.Ny, gc.Ny, j, cj[0], ay[0], cj[1], ay[1]);
+  ck[0] = tr.kc0[k]; ck[1] = tr.kc1[k]; az[0] = (T)tr.kw0[k]; az[1] = (T)tr.kw1[k];
+  T s = T(0);
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
-    if (wz[c] == 0.0) continue;
+    if (az[c] == T(0)) continue;
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      if (wy[b] == 0.0) continue;
+      if (ay[b] == T(0)) continue;
+      T row = T(0);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        if (wx[a] == 0.0) continue;
-        s += wx[a] * wy[b] * wz[c] * (double)ec[gidx(gc, ci[a], cj[b], ck[c])];
+        if (ax[a] == T(0)) continue;
+        row += ax[a] * ec[gidx(gc, ci[a], cj[b], ck[c])];
       }
+      s += (ay[b] * az[c]) * row;
     }
   }
   const int64_t o = gidx(gf, i, j, k);
-  x[o] = (T)((double)x[o] + s);
+  x[o] += s;
 }
 
 }  // namespace
@@ -200,6 +218,15 @@ cudaError_t launch_residual_mixed(const Grid& g, const double* C, const double* 
   dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
   if (partials && (int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
   k_residual<double, 1><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, nullptr, r32, e32, partials); count_launches(1);
+  if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const Grid& g, const double* C, const double* x, double* y,
+                         double* partials, int cap, int* nblocks, cudaStream_t st) {
+  dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
+  if ((int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
+  k_residual<double, 2><<<grd, dim3(32, 4), 0, st>>>(g, C, nullptr, x, y, nullptr, nullptr, partials); count_launches(1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
   return cudaGetLastError();
 }

@@ -302,3 +302,31 @@ def test_inverted_element(torch):
     with pytest.raises(m.MCWindError) as e:
         plan.assemble(X, Y, Zd)
     assert e.value.code == m.MCWIND_EGEOM
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", [m.PREC_F64, m.PREC_MIXED])
+def test_cg_accelerated_solve(torch, name, precision):
+    """V-cycle-preconditioned CG reaches the same discrete solution, in no
+    more cycles than the plain multigrid iteration."""
+    c, plan, (X, Y, Z, u0), H = setup(torch, name, precision=precision, coarsest_max=1024,
+                                      accel=m.ACCEL_CG)
+    lam, st = plan.solve(u0, rtol=1e-12, max_cycles=120)
+    assert st.status == m.MCWIND_OK and st.rel_res <= 1e-12, st.history()
+    if name not in _lam_ref:
+        _lam_ref[name] = oracle.solve(c)
+    assert rel(lam.cpu().numpy().ravel(), _lam_ref[name]) <= 1e-10
+    _, plan_mg, _, _ = setup(torch, name, precision=precision, coarsest_max=1024)
+    _, st_mg = plan_mg.solve(u0, rtol=1e-12, max_cycles=120)
+    assert st.cycles <= st_mg.cycles, (st.cycles, st_mg.cycles)
+
+
+def test_cg_warm_start(torch):
+    c, plan, (X, Y, Z, u0), _ = setup(torch, "ragged", precision=m.PREC_MIXED, coarsest_max=1024,
+                                      accel=m.ACCEL_CG)
+    lam, st_cold = plan.solve(u0, rtol=1e-10)
+    u0b = torch.from_numpy(synth.perturb_wind(c.u0, 0)).to("cuda")
+    lam_w, st_warm = plan.solve(u0b, lam=lam.clone(), rtol=1e-10, warm=True)
+    lam_c, st_c = plan.solve(u0b, rtol=1e-10)
+    assert st_warm.status == m.MCWIND_OK and st_warm.cycles < st_c.cycles
+    assert rel(lam_w.cpu().numpy(), lam_c.cpu().numpy()) <= 1e-8

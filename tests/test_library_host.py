@@ -55,6 +55,7 @@ def test_plan_rejects_bad_sizes(args):
     dict(opt=dict(precision=3)), dict(opt=dict(nu_pre=0, nu_post=0)),
     dict(opt=dict(coarsest_max=0)), dict(opt=dict(coarsest_max=100000)),
     dict(opt=dict(coarsen_rule=7)), dict(opt=dict(rhs_quad=2)),
+    dict(opt=dict(accel=2)), dict(opt=dict(accel=1, post_reverse=0)),
 ])
 def test_plan_rejects_bad_options(bad):
     a = bad.get("a", (1, 1, 1))
@@ -105,6 +106,13 @@ def test_planner_matches_oracle(name, maker, a, rule, cmax):
         for key in ("Nx", "Ny", "Nz", "hx", "hy", "kmap"):
             if key in want:
                 assert got[key] == want[key], (l, key, got, want)
+
+
+def test_cg_workspace_is_larger():
+    h3 = [5.0, 6.0, 7.0, 8.0]
+    _, ws0 = m.mcwind_plan_create(64, 48, 4, (1, 1, 1), 30.0, h3)
+    _, ws1 = m.mcwind_plan_create(64, 48, 4, (1, 1, 1), 30.0, h3, m.default_options(accel=1))
+    assert ws1 > ws0
 
 
 def test_full_domain_hierarchy_shape():
