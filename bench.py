@@ -37,6 +37,10 @@ CELLS = (3000, 3000, 15)
 RTOL = 1e-8
 SAMPLE_W = 160       # CPU baseline / reference window (cells per side)
 SAMPLE_I0, SAMPLE_J0 = 1420, 1420
+# FP64-pipe thread instructions per element of the element kernels (modal form), as
+# counted by ncu (smsp__sass_thread_inst_executed_op_fp64 / elements) on a small case
+FP64_OPS_STIFFNESS = 1213.0
+FP64_OPS_LOAD = 665.0
 
 
 def parse():
@@ -350,16 +354,32 @@ def main():
                            "warm_s": t_warm, "warm_cycles": st_warm.cycles,
                            "cold_rate": st_cold.rate}}
     prof_main = prof
+    prof_f64 = None
     if not args.no_f64_compare and prec == m.PREC_MIXED:
         del plan
+        torch.cuda.empty_cache()
+        # the same solves accelerated by conjugate gradients (one V-cycle per iteration)
+        pcg = m.Plan.for_case(case, precision=m.PREC_MIXED, accel=m.ACCEL_CG)
+        pcg.assemble(X, Y, Z)
+        lam.zero_()
+        time_solve(pcg, U0, False)
+        lam.zero_()
+        tcc, scc = time_solve(pcg, U0, False)
+        tcw, scw = time_solve(pcg, U0N, True)
+        tt["mixed_cg"] = {"cold_s": tcc, "cold_cycles": scc.cycles, "warm_s": tcw,
+                          "warm_cycles": scw.cycles, "cold_rate": scc.rate}
+        del pcg
         torch.cuda.empty_cache()
         p64 = m.Plan.for_case(case, precision=m.PREC_F64)
         p64.assemble(X, Y, Z)
         lam.zero_()
         time_solve(p64, U0, False)
         lam.zero_()
+        m.lib().mcwind_profile(p64.handle, 1, m._stream(None))
         t64c, s64c = time_solve(p64, U0, False)
         t64w, s64w = time_solve(p64, U0N, True)
+        prof_f64 = read_profile(m, p64)
+        m.lib().mcwind_profile(p64.handle, 0, m._stream(None))
         tt["f64"] = {"cold_s": t64c, "cold_cycles": s64c.cycles, "warm_s": t64w,
                      "warm_cycles": s64w.cycles, "cold_rate": s64c.rate}
         del p64
@@ -376,36 +396,44 @@ def main():
     plan_dims = (nx + 1, ny + 1, nz + 1)
     n_nodes = plan_dims[0] * plan_dims[1] * plan_dims[2]
     n_elem = nx * ny * nz
-    csize = 4 if prec == m.PREC_MIXED else 8
-    # algorithmic units of one launch of each class (derivations in the design doc)
-    algo = {
-        # bytes: 26 off-diagonal coefficients + 1/diagonal + f + x read + x write per free
-        # node of one column group
-        "smooth_fine": ("hbm", (27 * csize + 3 * csize) * n_free / 4.0),
-        "residual_fine": ("hbm", (27 * csize + 3 * csize) * n_free),
-        # float64 residual: 27 coefficients + f + x + r out (+ float32 r and e out when mixed)
-        "outer_residual": ("hbm", (27 * 8 + 3 * 8 + (8 if prec == m.PREC_MIXED else 0)) * n_free),
-        # FP64 operations of one element-parity launch (modal form): stiffness 1700 per
-        # element, load vector 975 per element
-        "assemble": ("alu", 1700.0 * n_elem / 8.0),
-        "rhs": ("alu", 975.0 * n_elem / 8.0),
-    }
+
+    def algo_units(cs, mixed):
+        """Algorithmic units of one launch of each class (derivations in the design doc)."""
+        return {
+            # bytes: 26 off-diagonal coefficients + 1/diagonal + f + x read + x write per
+            # free node of one column group
+            "smooth_fine": ("hbm", (27 * cs + 3 * cs) * n_free / 4.0),
+            "residual_fine": ("hbm", (27 * cs + 3 * cs) * n_free),
+            # float64 residual: 27 coefficients + f + x + r out (+ float32 r and e out when mixed)
+            "outer_residual": ("hbm", (27 * 8 + 3 * 8 + (8 if mixed else 0)) * n_free),
+            # FP64 operations of one element-parity launch (modal form, counted by ncu as
+            # FP64-pipe thread instructions per element): stiffness and load vector
+            "assemble": ("alu", FP64_OPS_STIFFNESS * n_elem / 8.0),
+            "rhs": ("alu", FP64_OPS_LOAD * n_elem / 8.0),
+        }
+
+    def roofs(profile, cs, mixed):
+        out = {}
+        for k, (bound, units) in algo_units(cs, mixed).items():
+            ms, n = profile[k]
+            if n == 0:
+                continue
+            per = ms / n / 1e3
+            if bound == "hbm":
+                ach = units / per / 1e9
+                out[k] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": ach / hbm_peak, "ms_per_launch": per * 1e3, "launches": n}
+            else:
+                ach = units / per / 1e12
+                out[k] = {"bound": "alu", "achieved": ach, "peak": fp64_peak,
+                          "unit": "T FP64 op/s", "frac": ach / fp64_peak,
+                          "ms_per_launch": per * 1e3, "launches": n}
+        return out
+
+    mixed = prec == m.PREC_MIXED
+    roof_kernels = roofs(prof_main, 4 if mixed else 8, mixed)
+    roof_f64 = roofs(prof_f64, 8, False) if prof_f64 else None
     dom = max((k for k in prof_main if prof_main[k][1] > 0), key=lambda k: prof_main[k][0])
-    roof_kernels = {}
-    for k, (bound, units) in algo.items():
-        ms, n = prof_main[k]
-        if n == 0:
-            continue
-        per = ms / n / 1e3
-        if bound == "hbm":
-            ach = units / per / 1e9
-            roof_kernels[k] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                               "frac": ach / hbm_peak, "ms_per_launch": per * 1e3, "launches": n}
-        else:
-            ach = units / per / 1e12
-            roof_kernels[k] = {"bound": "alu", "achieved": ach, "peak": fp64_peak,
-                               "unit": "T FP64 op/s", "frac": ach / fp64_peak,
-                               "ms_per_launch": per * 1e3, "launches": n}
     dom_roof = dict(roof_kernels.get(dom, {"bound": None}))
     dom_roof["kernel"] = dom
     dom_roof["traffic"] = None
@@ -442,6 +470,7 @@ def main():
         "wall_s": wall,
         "roofline": dom_roof,
         "roofline_kernels": roof_kernels,
+        "roofline_kernels_f64_solve": roof_f64,
         "profile_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof_main.items() if v[1]},
         "e2e": e2e,
         "cpu_baseline": cpu,

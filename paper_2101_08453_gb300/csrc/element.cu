@@ -128,11 +128,6 @@ __device__ __forceinline__ bool elem_of_thread(int nx, int ny, int nz, int cls, 
   return i < nx && j < ny && k < nz;
 }
 
-// sigma_q(g): product over the bits b of q of (+1 if bit b of g is set, else -1)
-__host__ __device__ constexpr double sgn(int q, int g) {
-  return ((q & 1) && !(g & 1) ? -1.0 : 1.0) * ((q & 2) && !(g & 2) ? -1.0 : 1.0) *
-         ((q & 4) && !(g & 4) ? -1.0 : 1.0);
-}
 __host__ __device__ constexpr int popc3(int q) { return (q & 1) + ((q >> 1) & 1) + ((q >> 2) & 1); }
 // index of the symmetric 3x3 component (a, b) in (00, 01, 02, 11, 12, 22)
 __host__ __device__ constexpr int sym6(int a, int b) {
@@ -167,11 +162,8 @@ __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny
   if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
   Geo G;
   load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+  // C_g = adj D adj^T / det at the 8 Gauss points (6 symmetric components)
   double Ch[8][6];
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) Ch[q][c] = 0.0;
   bool bad = false;
 #pragma unroll
   for (int gp = 0; gp < 8; ++gp) {
@@ -188,16 +180,23 @@ __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny
       aD[r][1] = adj[r][1] * d1;
       aD[r][2] = adj[r][2] * d2;
     }
-    double c6[6];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int t = r; t < 3; ++t)
-        c6[sym6(r, t)] = (aD[r][0] * adj[t][0] + aD[r][1] * adj[t][1] + aD[r][2] * adj[t][2]) * inv;
+        Ch[gp][sym6(r, t)] =
+            (aD[r][0] * adj[t][0] + aD[r][1] * adj[t][1] + aD[r][2] * adj[t][2]) * inv;
+  }
+  // sign sums over the Gauss points: sum_g sigma_q(g) C_g = (-1)^|q| (W C)[q]
+  // (the sign is applied where the sums are used)
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+  for (int c = 0; c < 6; ++c) {
+    double v[8];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) Ch[q][c] += sgn(q, gp) * c6[c];
+    for (int gp = 0; gp < 8; ++gp) v[gp] = Ch[gp][c];
+    wht8(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Ch[q][c] = v[q];
   }
   if (bad) atomicOr(flag, 1);
   // K~ = D K^ D / 64 (D[S] = (-1)^|S|); row and column 0 vanish
@@ -214,7 +213,8 @@ __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
           if (!((T >> b) & 1)) continue;
-          v += Ch[(S & ~(1 << a)) ^ (T & ~(1 << b))][sym6(a, b)];
+          const int q = (S & ~(1 << a)) ^ (T & ~(1 << b));
+          v += (popc3(q) & 1) ? -Ch[q][sym6(a, b)] : Ch[q][sym6(a, b)];
         }
       }
       const int e = popc3(S) + popc3(T);
@@ -277,21 +277,24 @@ __device__ __forceinline__ void weak_div_elem(const Geo& G, int quad, const Vsrc
   }
   double wh[8][3];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) wh[q][0] = wh[q][1] = wh[q][2] = 0.0;
-#pragma unroll
   for (int gp = 0; gp < 8; ++gp) {
     double xi[3], J[3][3], adj[3][3], v[3];
     gauss_xi(gp, xi);
     jacobian_at(G, xi, J);
     adjugate(J, adj);
     vsrc(gp, xi, v);
-    double w[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) w[r] = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
+    for (int r = 0; r < 3; ++r) wh[gp][r] = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
+  }
+  // sign sums over the Gauss points, (-1)^|q| (W w)[q] (sign applied below)
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+  for (int r = 0; r < 3; ++r) {
+    double t[8];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) wh[q][r] += sgn(q, gp) * w[r];
+    for (int gp = 0; gp < 8; ++gp) t[gp] = wh[gp][r];
+    wht8(t);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) wh[q][r] = (popc3(q) & 1) ? -t[q] : t[q];
   }
   // f~[S] = (-1)^|S| f^[S] / 8, then out = W f~
 #pragma unroll
