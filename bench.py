@@ -41,6 +41,11 @@ SAMPLE_I0, SAMPLE_J0 = 1420, 1420
 # counted by ncu (smsp__sass_thread_inst_executed_op_fp64 / elements) on a small case
 FP64_OPS_STIFFNESS = 1213.0
 FP64_OPS_LOAD = 665.0
+# DRAM bytes (read + write) per unit of a launch, from one ncu capture of the
+# 600x600x15 case (profiles/k_gs_float_600x600x15.md), scaled by the units of
+# the full launch: FP32 smoother, bytes per node of the column group.
+TRAFFIC_PER_UNIT = {"smooth_fine": (142.3, "ncu dram__bytes_read+write at 600x600x15, "
+                                           "scaled by the column-group nodes")}
 
 
 def parse():
@@ -437,6 +442,10 @@ def main():
     dom_roof = dict(roof_kernels.get(dom, {"bound": None}))
     dom_roof["kernel"] = dom
     dom_roof["traffic"] = None
+    if dom in TRAFFIC_PER_UNIT and mixed:
+        per_unit, how = TRAFFIC_PER_UNIT[dom]
+        dom_roof["traffic"] = per_unit * n_free / 4.0
+        dom_roof["traffic_source"] = how
     dom_roof["peak_source"] = ("measured: MEASURED_PEAKS.json hbm_gbs (burst copy)"
                                if dom_roof.get("bound") == "hbm"
                                else "measured: FP64 FMA issue rate of this GB300, 5.81e11/s")
