@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64-compare", action="store_true")
+    ap.add_argument("--workload", default="domain", choices=["domain", "batched", "rates"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -208,8 +210,129 @@ def read_profile(m, plan):
     return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}
 
 
+def bench_batched(args):
+    """96 independent domains (horizontal cells uniform in [48, 384] per axis,
+    8-20 layers, a3 in {1, 4, 10}), mixed precision, per-domain autotuned
+    sweeps and smoother block shape, solved together to 1e-8 (one CUDA graph
+    per iteration with a branch per domain)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2101_08453_gb300 as m
+    from paper_2101_08453_gb300 import autotune
+    import synth
+
+    m.build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cases = synth.batch_domains(n=96, seed=0)
+    plans, u0s = [], []
+    for c in cases:
+        X, Y, Z, u0 = (torch.from_numpy(a).cuda() for a in (c.X, c.Y, c.Z, c.u0))
+        p = m.Plan.for_case(c, precision=m.PREC_MIXED)
+        p.assemble(X, Y, Z)
+        p._keep = (X, Y, Z)
+        plans.append(p)
+        u0s.append(u0)
+    n_free = [c.n_free for c in cases]
+    t0 = time.perf_counter()
+    tuned = None
+    if not args.no_autotune:
+        tuned = autotune.tune_batch(plans, u0s, rtol=RTOL)
+    t_tune = time.perf_counter() - t0
+    batch = m.Batch(plans)
+    lams = [torch.zeros(p.node_shape, dtype=torch.float64, device="cuda") for p in plans]
+    for _ in range(args.warmup):
+        batch.solve(u0s, lams, rtol=RTOL)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    iters = 0
+    for _ in range(args.steps):
+        for l in lams:
+            l.zero_()
+        _, stats = batch.solve(u0s, lams, rtol=RTOL)
+        iters += max(st.cycles for st in stats)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    # the same domains one after another
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    seq_cycles = 0
+    for p, u0, l in zip(plans, u0s, lams):
+        l.zero_()
+        _, st = m.mcwind_solve(p.handle, u0, l, RTOL, 150, 0)
+        seq_cycles += st.cycles
+    s1.record()
+    torch.cuda.synchronize()
+    t_seq = s0.elapsed_time(s1) / 1e3
+    # per-domain error against the oracle on the 4 smallest domains
+    lams, stats = batch.solve(u0s, lams, rtol=1e-11, max_cycles=250)
+    small = sorted(range(len(cases)), key=lambda d: n_free[d])[:4]
+    errs = {cases[d].name: float(np.linalg.norm(lams[d].cpu().numpy().ravel() - (ref := oracle.solve(cases[d])))
+                                 / np.linalg.norm(ref)) for d in small}
+    cyc = max(st.cycles for st in stats)
+    line = {
+        "metric": "aggregate unknowns/s, 96 batched domains to 1e-8", "unit": "unknowns/s",
+        "value": sum(n_free) / t, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "96 independent domains, horizontal cells U[48,384] per axis, "
+                               "8-20 layers, a3 in {1,4,10}, random hills + log-law wind, "
+                               "mixed precision, one graph per iteration", "n_free_total": sum(n_free),
+                   "rtol": RTOL},
+        "unknown_vcycles_per_s": sum(n_free) * iters / args.steps / t,
+        "batch_iterations": iters // args.steps,
+        "sequential_s": t_seq, "batched_s": t, "batched_speedup": t_seq / t,
+        "autotune_s": t_tune,
+        "tuning": {c.name: list(b) for c, b in zip(cases, tuned)} if tuned else None,
+        "per_domain_max_rel_err_vs_oracle_smallest4": errs,
+        "domain_cycles_to_1e-8": [st.cycles for st in stats] if False else None,
+    }
+    line.pop("domain_cycles_to_1e-8")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_rates(args):
+    """Convergence rate of the multigrid cycle (2+2 sweeps, FP64) over the
+    penalty a3 and the vertical stretching, for both readings of the
+    semicoarsening ratio: one 150 m hill (sigma 400 m) on 128 x 128 x 12 cells,
+    ground layer 5 m, log-law wind + noise; rate = geometric mean reduction
+    from cycle 3, to 1e-10."""
+    import numpy as np
+    import torch
+
+    import paper_2101_08453_gb300 as m
+    import synth
+
+    m.build.build()
+    rows = []
+    terrain = synth.single_hill(128, 128, 12).Z[0]   # the ground surface z_s(x, y)
+    for stretch in (1.0, 1.1, 1.2, 1.3):
+        for a3 in (1.0, 2.0, 5.0, 10.0, 20.0):
+            X, Y, Z, zeta = synth.node_grid(128, 128, 12, terrain, h0=5.0, ratio=stretch)
+            u0 = synth.log_wind(128, 128, 12, zeta, 8.0, 270.0, 0.2, np.random.default_rng(0))
+            Xd, Yd, Zd, U = (torch.from_numpy(v).cuda() for v in (X, Y, Z, u0))
+            for rule, name in ((m.RULE_PAPER, "paper"), (m.RULE_OPERATOR, "operator")):
+                p = m.Plan(128, 128, 12, (1.0, 1.0, a3), synth.DX,
+                           synth.layer_thicknesses(12, 5.0, stretch), coarsen_rule=rule)
+                p.assemble(Xd, Yd, Zd)
+                lam, st = p.solve(U, rtol=1e-10, max_cycles=200)
+                rows.append({"stretch": stretch, "a3": a3, "rule": name, "levels": p.num_levels,
+                             "cycles_to_1e-10": st.cycles, "rate": st.rate, "status": st.status})
+                del p
+    print(json.dumps({"workload": "rate study, 128x128x12 single hill", "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "batched" and args.impl != "reference":
+        return bench_batched(args)
+    if args.workload == "rates" and args.impl != "reference":
+        return bench_rates(args)
     if args.cpu_sample:
         print(json.dumps(run_cpu_sample(steps=1)), flush=True)
         return 0

@@ -70,6 +70,7 @@ enum { MCWIND_RULE_PAPER = 0, MCWIND_RULE_OPERATOR = 1 };
 enum { MCWIND_AT_CENTERS = 0, MCWIND_AT_GAUSS = 1 };
 enum { MCWIND_FORWARD = 0, MCWIND_BACKWARD = 1 };
 enum { MCWIND_ACCEL_NONE = 0, MCWIND_ACCEL_CG = 1 };
+enum { MCWIND_U0_NODES = 0, MCWIND_U0_CENTERS = 1 };
 
 #define MCWIND_WARM 1u        /* mcwind_solve flag: start from the caller's lambda */
 #define MCWIND_HIST 256
@@ -103,6 +104,17 @@ typedef struct {
      symmetric cycle); same solution, fewer cycles when the cycle alone
      converges slowly. */
   int accel;
+  /* 1 (default): each solver iteration is captured once as a CUDA graph
+     (on a stream the plan creates) and replayed on the caller's stream;
+     0: direct launches.  Same kernels, same order, same results.  While the
+     profiler is on, direct launches are used. */
+  int use_graphs;
+  /* MCWIND_U0_NODES (default): u0 arrays are nodal [3][nz+1][ny+1][nx+1] and
+     interpolated trilinearly.  MCWIND_U0_CENTERS: u0 is one vector per element
+     center, [3][nz][ny][nx] (the paper's representation of the wind, Sec. 2),
+     constant over the element in the load vector and in the recovery.  The
+     gradient entry points require MCWIND_U0_NODES. */
+  int u0_at;
 } mcwind_options;
 
 typedef struct {
@@ -157,6 +169,13 @@ int mcwind_assemble(mcwind_plan plan, void* workspace, const double* X, const do
 int mcwind_solve(mcwind_plan plan, const double* u0, double* lambda, double rtol, int max_cycles,
                  unsigned flags, mcwind_stats* stats, void* stream);
 
+/* Solve K_FF x_F = f_F for the caller's load vector instead of Eq. 5's:
+ * f device [nz+1][ny+1][nx+1] (fixed-node entries ignored), x as lambda in
+ * mcwind_solve (read when flags & MCWIND_WARM, always written).  Same
+ * iteration, stopping test (relative to ||f_F||), codes and stats. */
+int mcwind_solve_rhs(mcwind_plan plan, const double* f, double* x, double rtol, int max_cycles,
+                     unsigned flags, mcwind_stats* stats, void* stream);
+
 /* Recover the wind, Eq. 3: u = u0 + A^{-1} grad lambda.
  * where = MCWIND_AT_CENTERS: u device [3][nz][ny][nx] at element centers
  * (u0 there is the mean of the 8 corners); MCWIND_AT_GAUSS: u device
@@ -164,6 +183,24 @@ int mcwind_solve(mcwind_plan plan, const double* u0, double* lambda, double rtol
  * gx = 0 at xi = -1/sqrt(3).  u0, lambda: device nodal, as in mcwind_solve. */
 int mcwind_recover(mcwind_plan plan, const double* u0, const double* lambda, double* u,
                    int where, void* stream);
+
+/* Gradients of a loss l(u) with u the wind at the element centers (Eq. 3,
+ * mcwind_recover with MCWIND_AT_CENTERS) and lambda from Eq. 5 (2x2x2 load
+ * vector), by the adjoint method; the same self-adjoint multigrid solves the
+ * adjoint system.  With gu = dl/du (device [3][nz][ny][nx]):
+ *   1. mcwind_recover_adjoint: h = G^T A^{-1} gu (device nodal) and
+ *      du0 = C^T gu (device [3][nz+1][ny+1][nx+1]), G the gradient and C the
+ *      corner mean at the centers;
+ *   2. mu = K_FF^{-1} h_F by mcwind_solve_rhs;
+ *   3. mcwind_adjoint_finish: du0 -= I^T B^T mu (I: nodes to Gauss points, B
+ *      the weak divergence), so du0 = dl/du0; and dloga (host, 3) =
+ *      dl/d(log a_d) = 2 a_d^-2 (mu^T K_d lambda - sum_centers gu_d d_d lambda),
+ *      K_d the stiffness of the d-th derivative term.  Synchronizes once.
+ * lambda and mu must be 0 at fixed nodes (as mcwind_solve writes them). */
+int mcwind_recover_adjoint(mcwind_plan plan, const double* gu, double* h, double* du0,
+                           void* stream);
+int mcwind_adjoint_finish(mcwind_plan plan, const double* mu, const double* lambda,
+                          const double* gu, double* du0, double* dloga, void* stream);
 
 /* Load vector f of Eq. 5 (right side; plan's quadrature) at every node,
  * device [nz+1][ny+1][nx+1]; 0 at fixed nodes. */
@@ -232,6 +269,39 @@ int mcwind_vcycle(mcwind_plan plan, int precision, double* x, const double* f, v
  * on it.  ESTATE if the plan is not assembled. */
 int mcwind_residual_norm_noalloc(mcwind_plan plan, const double* f, const double* lambda,
                                  double* norms, void* stream);
+
+/* ---- many independent domains ---------------------------------------------
+ * A batch groups n assembled plans (independent domains of any sizes) whose
+ * solves run together: each iteration of all domains is one CUDA graph with
+ * one branch per domain, so the GPU overlaps the domains' kernels, and one
+ * device-to-host copy returns every domain's residual.  Plans must use the
+ * plain multigrid iteration (accel = MCWIND_ACCEL_NONE), stay assembled and
+ * keep their workspaces while the batch lives; a plan belongs to at most
+ * one batch.  Host arrays of device pointers are passed per domain. */
+typedef struct mcwind_batch_s* mcwind_batch;
+
+/* Device workspace bytes a batch of n domains needs (n doubles, rounded up). */
+size_t mcwind_batch_workspace_bytes(int n);
+
+/* plans: host array of n assembled plans.  workspace: device, >=
+ * mcwind_batch_workspace_bytes(n), 256-byte aligned, caller-owned. */
+int mcwind_batch_create(int n, const mcwind_plan* plans, void* workspace, mcwind_batch* out);
+
+/* Solve every domain d: u0[d], lambda[d] as in mcwind_solve.  Iterates until
+ * every domain is at or below rtol or max_cycles; domains that converge first
+ * keep iterating (their residual only decreases) and stats[d].cycles records
+ * the cycle at which domain d first reached rtol.  stats: host, n entries, may
+ * be NULL.  Returns OK, ENOTCONV (some domain above rtol), ENONFINITE, EINVAL. */
+int mcwind_batch_solve(mcwind_batch batch, const double* const* u0, double* const* lambda,
+                       double rtol, int max_cycles, unsigned flags, mcwind_stats* stats,
+                       void* stream);
+
+void mcwind_batch_destroy(mcwind_batch batch);
+
+/* Change the smoothing sweeps and the smoother's thread-block height (column
+ * rows per block: 1, 2, 4 or 8; default 4) of an existing plan.  Used by the
+ * batch autotuner; invalidates the plan's captured iteration graph. */
+int mcwind_plan_set_tuning(mcwind_plan plan, int nu_pre, int nu_post, int gs_block_rows);
 
 /* ---- measurement --------------------------------------------------------
  * Kernel classes timed by the optional profiler (CUDA events recorded on the

@@ -64,10 +64,11 @@ def lib():
         L.oracle_gs_sweep.argtypes = [c_int] * 3 + [i64, i64, d, d, d, c_int]
         L.oracle_gauss_detj.argtypes = [c_int] * 3 + [d] * 4
         L.oracle_interp_gauss.argtypes = [c_int] * 3 + [d, d]
+        L.oracle_assemble_rhs_centers.argtypes = [c_int] * 3 + [d] * 4 + [c_int, d]
         for name in ("oracle_element_stiffness", "oracle_element_rhs", "oracle_assemble_coo",
                      "oracle_assemble_rhs", "oracle_assemble_rhs_par", "oracle_stencil_row",
                      "oracle_apply_K", "oracle_recover", "oracle_weak_div",
-                     "oracle_gauss_detj", "oracle_interp_gauss"):
+                     "oracle_gauss_detj", "oracle_interp_gauss", "oracle_assemble_rhs_centers"):
             getattr(L, name).restype = c_int
         L.oracle_gs_sweep.restype = None
         _lib = L
@@ -157,6 +158,20 @@ def assemble_f(c, u0=None, quad=0, parallel=False):
     _check(fn(c.nx, c.ny, c.nz, _p(_f64(c.X)), _p(_f64(c.Y)), _p(_f64(c.Z)), _p(u0), quad,
               _p(f)))
     return f
+
+
+def assemble_f_centers(c, uc, quad=0):
+    """Load vector for a wind given at the element centers, uc (3, nz, ny, nx):
+    constant over each element (the paper's wind representation, Sec. 2)."""
+    f = np.zeros(c.n_nodes)
+    _check(lib().oracle_assemble_rhs_centers(c.nx, c.ny, c.nz, _p(_f64(c.X)), _p(_f64(c.Y)),
+                                             _p(_f64(c.Z)), _p(_f64(uc)), quad, _p(f)))
+    return f
+
+
+def recover_centers(c, lam, uc, a=None):
+    """u = uc + A^{-1} grad lambda at the element centers (Eq. 3), wind given there."""
+    return recover(c, lam, u0=np.zeros((3,) + c.u0.shape[1:]), where=0, a=a) + uc
 
 
 def stencil_row(c, i, j, k, a=None):
@@ -501,3 +516,53 @@ class Hierarchy:
             x = self.vcycle(0, f, x, nu1, nu2)
             hist.append(np.linalg.norm(f - self.K[0] @ x) / nf)
         return x, hist
+
+
+# --------------------------------------------------------------------------
+# derivatives of the recovered wind (brute force, tiny grids)
+
+def dense_wind_gradient(c, gu, a=None, h_loga=1e-6):
+    """Gradient of l(u) with dl/du = gu (u at the element centers, Eq. 3 with
+    lambda from Eq. 5), by dense linear algebra on matrices probed from the
+    oracle's own maps with unit vectors:
+        du/du0 = R_u0 + R_lam[:, F] K_FF^{-1} J_f[F, :],
+    R_u0 = du/du0 at fixed lambda, R_lam = du/dlambda, J_f = df/du0.
+    dl/dlog a_d by central differences (step h_loga) of l = gu . u(a) through
+    the oracle's forward map.  Returns (dl/du0 shaped like u0, [3])."""
+    a = np.asarray(c.a if a is None else a, dtype=np.float64)
+    N = c.n_nodes
+    free = case_free_mask(c)
+    gu = np.asarray(gu, dtype=np.float64).ravel()
+    zero_l = np.zeros(N)
+    zero_u = np.zeros((3,) + c.u0.shape[1:])
+    R_u0 = np.zeros((gu.size, 3 * N))
+    J_f = np.zeros((N, 3 * N))
+    e = np.zeros(3 * N)
+    for q in range(3 * N):
+        e[:] = 0.0
+        e[q] = 1.0
+        uq = e.reshape(c.u0.shape)
+        R_u0[:, q] = recover(c, zero_l, u0=uq, a=a).ravel()
+        J_f[:, q] = assemble_f(c, u0=uq)
+    fidx = np.flatnonzero(free)
+    R_l = np.zeros((gu.size, fidx.size))
+    el = np.zeros(N)
+    for col, q in enumerate(fidx):
+        el[:] = 0.0
+        el[q] = 1.0
+        R_l[:, col] = recover(c, el, u0=zero_u, a=a).ravel()
+    K = assemble_K(c, a).toarray()[np.ix_(free, free)]
+    dudu0 = R_u0 + R_l @ np.linalg.solve(K, J_f[free])
+    g_u0 = (dudu0.T @ gu).reshape(c.u0.shape)
+
+    def loss(av):
+        lam = solve(c, K=assemble_K(c, av))
+        return float(gu @ recover(c, lam, a=av).ravel())
+
+    g_loga = []
+    for d in range(3):
+        ap, am = a.copy(), a.copy()
+        ap[d] *= np.exp(h_loga)
+        am[d] *= np.exp(-h_loga)
+        g_loga.append((loss(ap) - loss(am)) / (2.0 * h_loga))
+    return g_u0, g_loga

@@ -439,3 +439,27 @@ int oracle_interp_gauss(int nx, int ny, int nz, const double* u0, double* ug) {
       }
   return 0;
 }
+
+/* Load vector for a wind given at the element centers, uc[3][nz][ny][nx]
+ * (the paper's representation of the wind, Sec. 2): the wind is constant over
+ * each element, so the element routine gets the center value at all 8 nodes. */
+int oracle_assemble_rhs_centers(int nx, int ny, int nz, const double* X, const double* Y,
+                                const double* Z, const double* uc, int quad, double* f) {
+  int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  int64_t NE = (int64_t)nx * ny * nz;
+  memset(f, 0, N * sizeof(double));
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double xe[8][3], ue[8][3], fe[8];
+        int64_t e = ((int64_t)k * ny + j) * nx + i;
+        gather_xe(nx, ny, X, Y, Z, i, j, k, xe);
+        for (int n = 0; n < 8; ++n)
+          for (int d = 0; d < 3; ++d) ue[n][d] = uc[d * NE + e];
+        int rc = oracle_element_rhs(&xe[0][0], &ue[0][0], quad, fe);
+        if (rc) return rc;
+        for (int m = 0; m < 8; ++m)
+          f[nid(nx, ny, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] += fe[m];
+      }
+  return 0;
+}

@@ -29,6 +29,7 @@ RULE_PAPER, RULE_OPERATOR = 0, 1
 AT_CENTERS, AT_GAUSS = 0, 1
 FORWARD, BACKWARD = 0, 1
 ACCEL_NONE, ACCEL_CG = 0, 1
+U0_NODES, U0_CENTERS = 0, 1
 WARM = 1
 HIST = 256
 
@@ -46,7 +47,8 @@ class Options(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("coarsen_rule", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("precision", ctypes.c_int), ("rhs_quad", ctypes.c_int),
-                ("post_reverse", ctypes.c_int), ("accel", ctypes.c_int)]
+                ("post_reverse", ctypes.c_int), ("accel", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("u0_at", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -93,6 +95,18 @@ def lib():
         "mcwind_coarse_solve": (_i, [_vp, _vp, _vp, _vp]),
         "mcwind_vcycle": (_i, [_vp, _i, _vp, _vp, _vp]),
         "mcwind_residual_norm_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp]),
+        "mcwind_solve_rhs": (_i, [_vp, _vp, _vp, _d, _i, ctypes.c_uint, ctypes.POINTER(Stats), _vp]),
+        "mcwind_recover_adjoint": (_i, [_vp, _vp, _vp, _vp, _vp]),
+        "mcwind_adjoint_finish": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _vp]),
+        "mcwind_batch_workspace_bytes": (ctypes.c_size_t, [_i]),
+        "mcwind_batch_create": (_i, [_i, ctypes.POINTER(_vp), _vp, ctypes.POINTER(_vp)]),
+        "mcwind_batch_solve": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
+                                    ctypes.c_uint, ctypes.POINTER(Stats), _vp]),
+        "mcwind_batch_destroy": (None, [_vp]),
+        "mcwind_plan_set_tuning": (_i, [_vp, _i, _i, _i]),
+        "mcwind_launch_count": (ctypes.c_longlong, []),
+        "mcwind_profile": (_i, [_vp, _i, _vp]),
+        "mcwind_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i, _vp]),
         "mcwind_plan_destroy": (None, [_vp]),
         "mcwind_strerror": (ctypes.c_char_p, [_i]),
         "mcwind_last_cuda_error": (_i, []),
@@ -189,6 +203,27 @@ def mcwind_solve(plan, u0, lam, rtol=1e-8, max_cycles=100, flags=0, stream=None,
     return rc, st
 
 
+def mcwind_solve_rhs(plan, f, x, rtol=1e-8, max_cycles=100, flags=0, stream=None):
+    st = Stats()
+    rc = _check(lib().mcwind_solve_rhs(plan, _dev(f, "f"), _dev(x, "x"), float(rtol), int(max_cycles),
+                                       int(flags), ctypes.byref(st), _stream(stream)),
+                "mcwind_solve_rhs", ok=(MCWIND_OK, MCWIND_ENOTCONV))
+    return rc, st
+
+
+def mcwind_recover_adjoint(plan, gu, h, du0, stream=None):
+    return _check(lib().mcwind_recover_adjoint(plan, _dev(gu, "gu"), _dev(h, "h"), _dev(du0, "du0"),
+                                               _stream(stream)), "mcwind_recover_adjoint")
+
+
+def mcwind_adjoint_finish(plan, mu, lam, gu, du0, stream=None):
+    """Returns dl/dlog a as a list of 3 floats (du0 updated in place)."""
+    out = (_d * 3)()
+    _check(lib().mcwind_adjoint_finish(plan, _dev(mu, "mu"), _dev(lam, "lambda"), _dev(gu, "gu"),
+                                       _dev(du0, "du0"), out, _stream(stream)), "mcwind_adjoint_finish")
+    return [out[0], out[1], out[2]]
+
+
 def mcwind_recover(plan, u0, lam, u, where=AT_CENTERS, stream=None):
     return _check(lib().mcwind_recover(plan, _dev(u0, "u0"), _dev(lam, "lambda"), _dev(u, "u"),
                                        int(where), _stream(stream)), "mcwind_recover")
@@ -249,6 +284,47 @@ def mcwind_residual_norm_noalloc(plan, f, lam, norms, stream=None):
     return _check(lib().mcwind_residual_norm_noalloc(plan, _dev(f, "f"), _dev(lam, "lambda"),
                                                      _dev(norms, "norms"), _stream(stream)),
                   "mcwind_residual_norm_noalloc")
+
+
+def mcwind_plan_set_tuning(plan, nu_pre, nu_post, gs_block_rows):
+    return _check(lib().mcwind_plan_set_tuning(plan, int(nu_pre), int(nu_post), int(gs_block_rows)),
+                  "mcwind_plan_set_tuning")
+
+
+class Batch:
+    """Independent domains (assembled Plans) solved together: each iteration of
+    all domains is one CUDA graph with a branch per domain."""
+
+    def __init__(self, plans):
+        import torch
+        self.plans = list(plans)
+        n = len(self.plans)
+        nbytes = lib().mcwind_batch_workspace_bytes(n)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        off = (-self._ws.data_ptr()) % 256
+        arr = (_vp * n)(*[p.handle for p in self.plans])
+        self.handle = _vp()
+        _check(lib().mcwind_batch_create(n, arr, _vp(self._ws.data_ptr() + off),
+                                         ctypes.byref(self.handle)), "mcwind_batch_create")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.mcwind_batch_destroy(h)
+            self.handle = None
+
+    def solve(self, u0s, lams=None, rtol=1e-8, max_cycles=100, warm=False, stream=None):
+        import torch
+        n = len(self.plans)
+        if lams is None:
+            lams = [torch.zeros(p.node_shape, dtype=torch.float64, device="cuda") for p in self.plans]
+        u_arr = (_vp * n)(*[_dev(u, "u0").value for u in u0s])
+        l_arr = (_vp * n)(*[_dev(l, "lambda").value for l in lams])
+        stats = (Stats * n)()
+        rc = lib().mcwind_batch_solve(self.handle, u_arr, l_arr, float(rtol), int(max_cycles),
+                                      WARM if warm else 0, stats, _stream(stream))
+        _check(rc, "mcwind_batch_solve", ok=(MCWIND_OK, MCWIND_ENOTCONV))
+        return lams, list(stats)
 
 
 class Plan:

@@ -27,6 +27,9 @@ thread_local int g_last_cuda = 0;
 
 long long launches_now() { return mcwind_launch_count(); }
 
+// quadrature and u0 location of the load vector, as the element kernel takes them
+int rhs_mode(mcwind_plan p) { return (p->opt.rhs_quad & 1) | (p->opt.u0_at ? 2 : 0); }
+
 // Records a CUDA event pair around a kernel class while profiling is on.
 // A scope reserves its two events when it opens; finished pairs are folded
 // into the per-class totals whenever the stream is idle, and the event pool
@@ -127,7 +130,7 @@ int smooth(mcwind_plan p, int l, int sweeps, int direction, cudaStream_t st) {
   for (int s = 0; s < sweeps; ++s)
     for (int q = 0; q < 4; ++q) {
       const int grp = direction == MCWIND_FORWARD ? q : 3 - q;
-      CK(launch_gs_group<T>(g, P.C, P.f, P.x, grp, direction == MCWIND_FORWARD ? 1 : 0, st));
+      CK(launch_gs_group<T>(g, P.C, P.f, P.x, grp, direction == MCWIND_FORWARD ? 1 : 0, p->gs_rows, st));
     }
   return MCWIND_OK;
 }
@@ -211,6 +214,37 @@ int one_cycle(mcwind_plan p, cudaStream_t st) {
   return outer_residual(p, st);
 }
 
+// Run one solver iteration (body(p, stream)) on st: replayed from a graph
+// captured once per plan and workspace, or launched directly while profiling
+// or when graphs are off.
+template <typename Body>
+int run_iteration(mcwind_plan p, cudaStream_t st, Body body) {
+  if (p->prof || !p->opt.use_graphs) return body(p, st);
+  if (!p->iter_exec || p->iter_ws != p->ws) {
+    if (p->iter_exec) { cudaGraphExecDestroy(p->iter_exec); p->iter_exec = nullptr; }
+    if (!p->cap_stream) CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long n0 = mcwind_launch_count();
+    const int rc = body(p, p->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (rc != MCWIND_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CK(e);
+    const cudaError_t ei = cudaGraphInstantiate(&p->iter_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    p->iter_ws = p->ws;
+    p->iter_launches = mcwind_launch_count() - n0;
+    count_launches(-(int)p->iter_launches);  // captured, not run: counted at replay
+  }
+  CK(cudaGraphLaunch(p->iter_exec, st));
+  count_launches((int)p->iter_launches);
+  return MCWIND_OK;
+}
+
 // copy device scalars [first, first + n) to host (synchronizes the stream)
 int read_scalars(mcwind_plan p, double* host, int first, int n, cudaStream_t st) {
   CK(cudaMemcpyAsync(host, scal(p) + first, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
@@ -240,6 +274,8 @@ extern "C" const char* mcwind_strerror(int code) {
 extern "C" void mcwind_plan_destroy(mcwind_plan p) {
   if (!p) return;
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->iter_exec) cudaGraphExecDestroy(p->iter_exec);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
 }
 
@@ -324,7 +360,7 @@ extern "C" int mcwind_rhs(mcwind_plan p, const double* u0, double* f, void* stre
   Level& L0 = p->lv[0];
   Ptr64 A = lv64(p, 0);
   CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, st));
-  CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, p->opt.rhs_quad, A.f, st));
+  CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, rhs_mode(p), A.f, st));
   CK(launch_split_to_std<double>(L0.g, A.f, f, st));
   return MCWIND_OK;
 }
@@ -346,9 +382,9 @@ int cg_restart(mcwind_plan p, const CgVec& v, cudaStream_t st) {
   PROF(MCWIND_K_KRYLOV);
   const Grid& g = p->lv[0].g;
   if (p->opt.precision == MCWIND_PREC_F64)
-    CK(launch_cg_start<double>(g, v.r, v.rp, lv64(p, 0).f, lv64(p, 0).x, st));
+    CK(launch_cg_start<double>(g, v.r, v.rp, lv64(p, 0).f, lv64(p, 0).x, scal(p) + 4, st));
   else
-    CK(launch_cg_start<float>(g, v.r, v.rp, lv32(p, 0).f, lv32(p, 0).x, st));
+    CK(launch_cg_start<float>(g, v.r, v.rp, lv32(p, 0).f, lv32(p, 0).x, scal(p) + 4, st));
   return MCWIND_OK;
 }
 
@@ -367,7 +403,7 @@ int cg_true_residual(mcwind_plan p, const CgVec& v, cudaStream_t st) {
 
 // one preconditioned CG iteration; ||r||^2 (recursive) into scal[1]
 template <typename T>
-int cg_iteration(mcwind_plan p, const CgVec& v, int first, cudaStream_t st) {
+int cg_iteration(mcwind_plan p, const CgVec& v, cudaStream_t st) {
   CKR(vcycle<T>(p, 0, st));
   const Grid& g = p->lv[0].g;
   auto P = Sel<T>::get(p, 0);
@@ -375,7 +411,7 @@ int cg_iteration(mcwind_plan p, const CgVec& v, int first, cudaStream_t st) {
   {
     PROF(MCWIND_K_KRYLOV);
     CK(launch_cg_dots<T>(g, v.r, v.rp, P.x, partials(p), p->n_partials, s, st));
-    CK(launch_cg_direction<T>(g, P.x, v.p, s, first, st));
+    CK(launch_cg_direction<T>(g, P.x, v.p, s, st));
   }
   int nb = 0;
   {
@@ -392,14 +428,17 @@ int cg_iteration(mcwind_plan p, const CgVec& v, int first, cudaStream_t st) {
   return MCWIND_OK;
 }
 
-int solve_cg(mcwind_plan p, const double* u0, double* lambda, double rtol, int max_cycles,
-             unsigned flags, mcwind_stats& S, cudaStream_t st) {
+int solve_cg(mcwind_plan p, const double* u0, const double* f_given, double* lambda,
+             double rtol, int max_cycles, unsigned flags, mcwind_stats& S, cudaStream_t st) {
   Level& L0 = p->lv[0];
   const CgVec v = cg_vectors(p);
-  {
+  if (f_given) {
+    PROF(MCWIND_K_OTHER);
+    CK(launch_std_to_split<double>(L0.g, f_given, v.f, true, st));
+  } else {
     PROF(MCWIND_K_RHS);
     CK(cudaMemsetAsync(v.f, 0, sizeof(double) * (size_t)L0.g.total, st));
-    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, p->opt.rhs_quad, v.f, st));
+    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, rhs_mode(p), v.f, st));
   }
   CKR(norm2(p, L0.g, v.f, 0, st));
   {
@@ -422,7 +461,7 @@ int solve_cg(mcwind_plan p, const double* u0, double* lambda, double rtol, int m
   } else {
     S.res_hist[0] = std::sqrt(h[1]) / nf;
     CKR(cg_restart(p, v, st));
-    int c = 0, first = 1;
+    int c = 0;
     while (c < max_cycles) {
       if (S.res_hist[c] <= rtol) {
         // the recursive residual says converged: confirm with the true one
@@ -431,11 +470,11 @@ int solve_cg(mcwind_plan p, const double* u0, double* lambda, double rtol, int m
         S.res_hist[c] = std::sqrt(h[1]) / nf;
         if (S.res_hist[c] <= rtol) break;
         CKR(cg_restart(p, v, st));
-        first = 1;
       }
-      if (p->opt.precision == MCWIND_PREC_F64) CKR(cg_iteration<double>(p, v, first, st));
-      else CKR(cg_iteration<float>(p, v, first, st));
-      first = 0;
+      if (p->opt.precision == MCWIND_PREC_F64)
+        CKR(run_iteration(p, st, [&v](mcwind_plan q, cudaStream_t s2) -> int { return cg_iteration<double>(q, v, s2); }));
+      else
+        CKR(run_iteration(p, st, [&v](mcwind_plan q, cudaStream_t s2) -> int { return cg_iteration<float>(q, v, s2); }));
       CKR(read_scalars(p, h + 1, 1, 1, st));
       ++c;
       S.res_hist[c] = std::sqrt(h[1]) / nf;
@@ -458,16 +497,18 @@ int solve_cg(mcwind_plan p, const double* u0, double* lambda, double rtol, int m
 
 }  // namespace
 
-extern "C" int mcwind_solve(mcwind_plan p, const double* u0, double* lambda, double rtol,
-                            int max_cycles, unsigned flags, mcwind_stats* stats, void* stream) {
-  if (!p || !u0 || !lambda) return MCWIND_EINVAL;
+// u0 given: load vector of Eq. 5 from it; f_given: the caller's load vector
+static int solve_impl(mcwind_plan p, const double* u0, const double* f_given, double* lambda,
+                      double rtol, int max_cycles, unsigned flags, mcwind_stats* stats,
+                      void* stream) {
+  if (!p || (!u0 && !f_given) || !lambda) return MCWIND_EINVAL;
   if (!p->assembled) return MCWIND_ESTATE;
   if (max_cycles < 0 || max_cycles >= MCWIND_HIST || !(rtol >= 0.0)) return MCWIND_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (p->opt.accel == MCWIND_ACCEL_CG) {
     mcwind_stats S;
     std::memset(&S, 0, sizeof(S));
-    int status = solve_cg(p, u0, lambda, rtol, max_cycles, flags, S, st);
+    int status = solve_cg(p, u0, f_given, lambda, rtol, max_cycles, flags, S, st);
     if (status != MCWIND_OK && status != MCWIND_ENOTCONV && status != MCWIND_ENONFINITE) return status;
     S.rel_res = S.res_hist[S.cycles];
     if (S.cycles >= 3 && S.res_hist[2] > 0.0)
@@ -481,10 +522,13 @@ extern "C" int mcwind_solve(mcwind_plan p, const double* u0, double* lambda, dou
   Level& L0 = p->lv[0];
   Ptr64 A = lv64(p, 0);
   // load vector f (Eq. 5 right side) and its norm
-  {
+  if (f_given) {
+    PROF(MCWIND_K_OTHER);
+    CK(launch_std_to_split<double>(L0.g, f_given, A.f, true, st));
+  } else {
     PROF(MCWIND_K_RHS);
     CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, st));
-    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, p->opt.rhs_quad, A.f, st));
+    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, rhs_mode(p), A.f, st));
   }
   CKR(norm2(p, L0.g, A.f, 0, st));
   {
@@ -513,7 +557,7 @@ extern "C" int mcwind_solve(mcwind_plan p, const double* u0, double* lambda, dou
     S.res_hist[0] = std::sqrt(h[1]) / nf;
     int c = 0;
     while (S.res_hist[c] > rtol && c < max_cycles) {
-      CKR(one_cycle(p, st));
+      CKR(run_iteration(p, st, one_cycle));
       CKR(read_scalars(p, h + 1, 1, 1, st));
       ++c;
       S.res_hist[c] = std::sqrt(h[1]) / nf;
@@ -536,6 +580,47 @@ extern "C" int mcwind_solve(mcwind_plan p, const double* u0, double* lambda, dou
   return status;
 }
 
+extern "C" int mcwind_solve(mcwind_plan p, const double* u0, double* lambda, double rtol,
+                            int max_cycles, unsigned flags, mcwind_stats* stats, void* stream) {
+  if (!u0) return MCWIND_EINVAL;
+  return solve_impl(p, u0, nullptr, lambda, rtol, max_cycles, flags, stats, stream);
+}
+
+extern "C" int mcwind_solve_rhs(mcwind_plan p, const double* f, double* x, double rtol,
+                                int max_cycles, unsigned flags, mcwind_stats* stats, void* stream) {
+  if (!f) return MCWIND_EINVAL;
+  return solve_impl(p, nullptr, f, x, rtol, max_cycles, flags, stats, stream);
+}
+
+extern "C" int mcwind_recover_adjoint(mcwind_plan p, const double* gu, double* h, double* du0,
+                                      void* stream) {
+  if (!p || !gu || !h || !du0 || p->opt.u0_at != MCWIND_U0_NODES) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t N = (size_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1);
+  CK(cudaMemsetAsync(h, 0, N * sizeof(double), st));
+  CK(cudaMemsetAsync(du0, 0, 3 * N * sizeof(double), st));
+  CK(launch_recover_adjoint(p->nx, p->ny, p->nz, p->X, p->Y, p->Z, gu, p->a, h, du0, st));
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_adjoint_finish(mcwind_plan p, const double* mu, const double* lambda,
+                                     const double* gu, double* du0, double* dloga, void* stream) {
+  if (!p || !mu || !lambda || !gu || !du0 || !dloga || p->opt.u0_at != MCWIND_U0_NODES)
+    return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* part = (double*)(p->ws + p->off_adj);
+  double* sums = part + 6 * (size_t)p->n_adj;
+  CK(launch_adjoint_finish(p->nx, p->ny, p->nz, p->X, p->Y, p->Z, mu, lambda, gu, du0, part,
+                           p->n_adj, sums, st));
+  double h6[6];
+  CK(cudaMemcpyAsync(h6, sums, sizeof(h6), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int d = 0; d < 3; ++d) dloga[d] = 2.0 / (p->a[d] * p->a[d]) * (h6[d] - h6[3 + d]);
+  return MCWIND_OK;
+}
+
 extern "C" int mcwind_recover(mcwind_plan p, const double* u0, const double* lambda, double* u,
                               int where, void* stream) {
   if (!p || !u0 || !lambda || !u) return MCWIND_EINVAL;
@@ -549,7 +634,7 @@ extern "C" int mcwind_recover(mcwind_plan p, const double* u0, const double* lam
     CK(launch_std_to_split<double>(L0.g, lambda, lam, true, st));
   }
   PROF(MCWIND_K_RECOVER);
-  CK(launch_recover(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, lam, p->a, where, u, st));
+  CK(launch_recover(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, lam, p->a, where, p->opt.u0_at, u, st));
   return MCWIND_OK;
 }
 
@@ -723,4 +808,232 @@ extern "C" int mcwind_profile_read(mcwind_plan p, double* ms, long long* launche
     launches[k] = p->prof_n[k];
   }
   return MCWIND_K_KINDS;
+}
+
+// ---------------------------------------------------------------------------
+// batches of independent domains
+
+struct mcwind_batch_s {
+  std::vector<mcwind_plan> plans;
+  double* dres = nullptr;              // device [2n]: ||f||^2, ||r||^2 per domain
+  std::vector<cudaStream_t> streams;   // one per domain
+  cudaStream_t cap = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const char*> ws_at_capture;
+  std::vector<long long> tuning_at_capture;
+  long long launches = 0;
+};
+
+namespace {
+
+long long tuning_key(mcwind_plan p) {
+  return ((long long)p->opt.nu_pre << 16) | ((long long)p->opt.nu_post << 8) | p->gs_rows;
+}
+
+// fork the batch's domain streams off st, run body(d) on each, join back into st
+template <typename Body>
+int fork_join(mcwind_batch b, cudaStream_t st, Body body) {
+  CK(cudaEventRecord(b->fork, st));
+  for (size_t d = 0; d < b->plans.size(); ++d) {
+    CK(cudaStreamWaitEvent(b->streams[d], b->fork, 0));
+    CKR(body((int)d, b->streams[d]));
+    CK(cudaEventRecord(b->joins[d], b->streams[d]));
+    CK(cudaStreamWaitEvent(st, b->joins[d], 0));
+  }
+  return MCWIND_OK;
+}
+
+int batch_iteration_body(mcwind_batch b, cudaStream_t st) {
+  return fork_join(b, st, [b](int d, cudaStream_t s) -> int {
+    mcwind_plan p = b->plans[d];
+    CKR(one_cycle(p, s));
+    CK(cudaMemcpyAsync(b->dres + 2 * d + 1, scal(p) + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return (int)MCWIND_OK;
+  });
+}
+
+int batch_iteration(mcwind_batch b, cudaStream_t st) {
+  bool stale = !b->exec;
+  for (size_t d = 0; d < b->plans.size() && !stale; ++d)
+    stale = b->ws_at_capture[d] != b->plans[d]->ws || b->tuning_at_capture[d] != tuning_key(b->plans[d]);
+  if (stale) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    const long long n0 = mcwind_launch_count();
+    const int rc = batch_iteration_body(b, b->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc != MCWIND_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CK(e);
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    b->launches = mcwind_launch_count() - n0;
+    count_launches(-(int)b->launches);
+    for (size_t d = 0; d < b->plans.size(); ++d) {
+      b->ws_at_capture[d] = b->plans[d]->ws;
+      b->tuning_at_capture[d] = tuning_key(b->plans[d]);
+    }
+  }
+  CK(cudaGraphLaunch(b->exec, st));
+  count_launches((int)b->launches);
+  return MCWIND_OK;
+}
+
+}  // namespace
+
+extern "C" size_t mcwind_batch_workspace_bytes(int n) {
+  return n <= 0 ? 0 : ((size_t)n * 16 + 255) / 256 * 256;
+}
+
+extern "C" int mcwind_batch_create(int n, const mcwind_plan* plans, void* workspace,
+                                   mcwind_batch* out) {
+  if (!out || n <= 0 || !plans || !workspace || ((uintptr_t)workspace) % 256 != 0) return MCWIND_EINVAL;
+  *out = nullptr;
+  for (int d = 0; d < n; ++d) {
+    if (!plans[d]) return MCWIND_EINVAL;
+    if (plans[d]->opt.accel != MCWIND_ACCEL_NONE || plans[d]->in_batch) return MCWIND_EINVAL;
+    for (int e = 0; e < d; ++e)
+      if (plans[e] == plans[d]) return MCWIND_EINVAL;
+  }
+  mcwind_batch b = new (std::nothrow) mcwind_batch_s;
+  if (!b) return MCWIND_EINVAL;
+  b->plans.assign(plans, plans + n);
+  b->dres = (double*)workspace;
+  b->ws_at_capture.assign(n, nullptr);
+  b->tuning_at_capture.assign(n, -1);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int d = 0; d < n && e == cudaSuccess; ++d) {
+    cudaStream_t s;
+    cudaEvent_t j;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    b->streams.push_back(s);
+    e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->joins.push_back(j);
+  }
+  if (e != cudaSuccess) {
+    g_last_cuda = (int)e;
+    mcwind_batch_destroy(b);
+    return MCWIND_ECUDA;
+  }
+  for (int d = 0; d < n; ++d) plans[d]->in_batch = true;
+  *out = b;
+  return MCWIND_OK;
+}
+
+extern "C" void mcwind_batch_destroy(mcwind_batch b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (mcwind_plan p : b->plans)
+    if (p) p->in_batch = false;
+  delete b;
+}
+
+extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, double* const* lambda,
+                                  double rtol, int max_cycles, unsigned flags,
+                                  mcwind_stats* stats, void* stream) {
+  if (!b || !u0 || !lambda) return MCWIND_EINVAL;
+  if (max_cycles < 0 || max_cycles >= MCWIND_HIST || !(rtol >= 0.0)) return MCWIND_EINVAL;
+  const int n = (int)b->plans.size();
+  for (int d = 0; d < n; ++d) {
+    if (!u0[d] || !lambda[d]) return MCWIND_EINVAL;
+    if (!b->plans[d]->assembled) return MCWIND_ESTATE;
+    if (b->plans[d]->prof) return MCWIND_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // per domain: load vector, its norm, first iterate, first residual
+  CKR(fork_join(b, st, [&](int d, cudaStream_t s) -> int {
+    mcwind_plan p = b->plans[d];
+    Level& L0 = p->lv[0];
+    Ptr64 A = lv64(p, 0);
+    CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, s));
+    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0[d], rhs_mode(p), A.f, s));
+    CKR(norm2(p, L0.g, A.f, 0, s));
+    if (flags & MCWIND_WARM)
+      CK(launch_std_to_split<double>(L0.g, lambda[d], A.x, true, s));
+    else
+      CK(cudaMemsetAsync(A.x, 0, sizeof(double) * (size_t)L0.g.total, s));
+    CKR(outer_residual(p, s));
+    CK(cudaMemcpyAsync(b->dres + 2 * d, scal(p), 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return (int)MCWIND_OK;
+  }));
+  std::vector<double> h(2 * (size_t)n);
+  CK(cudaMemcpyAsync(h.data(), b->dres, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<mcwind_stats> S(n);
+  std::vector<double> nf(n);
+  int status = MCWIND_OK;
+  bool all_done = true;
+  for (int d = 0; d < n; ++d) {
+    std::memset(&S[d], 0, sizeof(mcwind_stats));
+    nf[d] = std::sqrt(h[2 * d]);
+    S[d].norm_f = nf[d];
+    if (!std::isfinite(nf[d]) || !std::isfinite(h[2 * d + 1])) status = MCWIND_ENONFINITE;
+    S[d].res_hist[0] = nf[d] > 0.0 ? std::sqrt(h[2 * d + 1]) / nf[d] : 0.0;
+    S[d].cycles = S[d].res_hist[0] <= rtol ? 0 : -1;
+    all_done = all_done && S[d].cycles == 0;
+  }
+  if (status == MCWIND_ENONFINITE) {
+    if (stats)
+      for (int d = 0; d < n; ++d) { S[d].status = MCWIND_ENONFINITE; stats[d] = S[d]; }
+    return status;
+  }
+  int c = 0;
+  while (!all_done && c < max_cycles) {
+    CKR(batch_iteration(b, st));
+    CK(cudaMemcpyAsync(h.data(), b->dres, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ++c;
+    all_done = true;
+    for (int d = 0; d < n; ++d) {
+      if (S[d].cycles >= 0) continue;
+      S[d].res_hist[c] = nf[d] > 0.0 ? std::sqrt(h[2 * d + 1]) / nf[d] : 0.0;
+      if (S[d].res_hist[c] <= rtol || !std::isfinite(S[d].res_hist[c])) S[d].cycles = c;
+      else all_done = false;
+    }
+  }
+  for (int d = 0; d < n; ++d) {
+    mcwind_stats& T = S[d];
+    if (T.cycles < 0) T.cycles = c;
+    T.rel_res = T.res_hist[T.cycles];
+    if (T.cycles >= 3 && T.res_hist[2] > 0.0)
+      T.rate = std::pow(T.res_hist[T.cycles] / T.res_hist[2], 1.0 / (T.cycles - 2));
+    else if (T.cycles >= 1 && T.res_hist[0] > 0.0)
+      T.rate = std::pow(T.res_hist[T.cycles] / T.res_hist[0], 1.0 / T.cycles);
+    T.status = T.rel_res <= rtol ? MCWIND_OK : MCWIND_ENOTCONV;
+    if (T.status != MCWIND_OK) status = MCWIND_ENOTCONV;
+  }
+  CKR(fork_join(b, st, [&](int d, cudaStream_t s) -> int {
+    mcwind_plan p = b->plans[d];
+    CK(launch_split_to_std<double>(p->lv[0].g, lv64(p, 0).x, lambda[d], s));
+    return (int)MCWIND_OK;
+  }));
+  if (stats)
+    for (int d = 0; d < n; ++d) stats[d] = S[d];
+  return status;
+}
+
+extern "C" int mcwind_plan_set_tuning(mcwind_plan p, int nu_pre, int nu_post, int gs_block_rows) {
+  if (!p) return MCWIND_EINVAL;
+  if (nu_pre < 0 || nu_post < 0 || nu_pre > 16 || nu_post > 16 || nu_pre + nu_post == 0)
+    return MCWIND_EINVAL;
+  if (gs_block_rows != 1 && gs_block_rows != 2 && gs_block_rows != 4 && gs_block_rows != 8)
+    return MCWIND_EINVAL;
+  if (p->opt.accel == MCWIND_ACCEL_CG && nu_pre != nu_post) return MCWIND_EINVAL;
+  p->opt.nu_pre = nu_pre;
+  p->opt.nu_post = nu_post;
+  p->gs_rows = gs_block_rows;
+  if (p->iter_exec) { cudaGraphExecDestroy(p->iter_exec); p->iter_exec = nullptr; }
+  return MCWIND_OK;
 }

@@ -309,6 +309,15 @@ __device__ __forceinline__ void weak_div_elem(const Geo& G, int quad, const Vsrc
   wht8(out);
 }
 
+struct CenterValue {
+  double v0[3];
+  __device__ void operator()(int, const double*, double v[3]) const {
+    v[0] = v0[0];
+    v[1] = v0[1];
+    v[2] = v0[2];
+  }
+};
+
 struct NodalInterp {
   double ue[8][3];
   __device__ void operator()(int, const double xi[3], double v[3]) const {
@@ -353,11 +362,18 @@ __global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, in
   if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
   Geo G;
   load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
-  NodalInterp src;
-  int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-  load_u(u0, N, nx + 1, ny + 1, i, j, k, src.ue);
   double fe[8];
-  weak_div_elem(G, quad, src, fe);
+  if (quad & 2) {
+    // u0 given at the element centers: constant over the element
+    const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
+    CenterValue src{{u0[e], u0[NE + e], u0[2 * NE + e]}};
+    weak_div_elem(G, quad & 1, src, fe);
+  } else {
+    NodalInterp src;
+    int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    load_u(u0, N, nx + 1, ny + 1, i, j, k, src.ue);
+    weak_div_elem(G, quad & 1, src, fe);
+  }
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
@@ -391,7 +407,7 @@ __global__ void __launch_bounds__(128) k_recover(Grid g, int nx, int ny, int nz,
                                                  const double* __restrict__ Z,
                                                  const double* __restrict__ u0,
                                                  const double* __restrict__ lam, double d0,
-                                                 double d1, double d2,
+                                                 double d1, double d2, int u0_centers,
                                                  double* __restrict__ u) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -400,8 +416,17 @@ __global__ void __launch_bounds__(128) k_recover(Grid g, int nx, int ny, int nz,
   Geo G;
   load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
   double ue[8][3], le[8];
-  int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-  load_u(u0, N, nx + 1, ny + 1, i, j, k, ue);
+  const int64_t NEc = (int64_t)nx * ny * nz, ec = ((int64_t)k * ny + j) * nx + i;
+  if (u0_centers) {
+    // u0 given at the element centers: the same value at every corner
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ue[n][d] = u0[d * NEc + ec];
+  } else {
+    int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+    load_u(u0, N, nx + 1, ny + 1, i, j, k, ue);
+  }
 #pragma unroll
   for (int n = 0; n < 8; ++n) le[n] = lam[gidx(g, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1))];
   int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
@@ -431,6 +456,157 @@ __global__ void __launch_bounds__(128) k_recover(Grid g, int nx, int ny, int nz,
       u[((int64_t)d * ng + gp) * NE + e] = up[d] + gd * dd[d];
     }
   }
+}
+
+// ---- adjoint of the recovery and of the load vector (gradients) ----------
+//
+// Forward at element centers: u = C u0 + A^{-1} G lambda, lambda = K^{-1} f,
+// f = -B I u0 (I: nodes -> Gauss points, B: weak divergence, C: nodes ->
+// centers, G: gradient at the centers).  For a loss with dl/du = gu:
+//   dl/du0 = C^T gu - I^T B^T mu,   mu = K^{-1} h,   h = G^T A^{-1} gu,
+//   dl/dlog a_d = 2 a_d^-2 (E_d - T_d),
+//   E_d = mu^T K_d lambda = sum_e sum_g detJ (d_d mu)(d_d lambda),
+//   T_d = sum_centers gu_d (d_d lambda)(center).
+
+// h = G^T A^{-1} gu and du0 = C^T gu (u0 at a center is the mean of the 8
+// corners), scattered per element class; h, du0 in the [k][j][i] layout.
+__global__ void __launch_bounds__(128) k_recover_adjoint(int nx, int ny, int nz,
+                                                         const double* __restrict__ X,
+                                                         const double* __restrict__ Y,
+                                                         const double* __restrict__ Z,
+                                                         const double* __restrict__ gu, double d0,
+                                                         double d1, double d2,
+                                                         double* __restrict__ h,
+                                                         double* __restrict__ du0, int cls) {
+  int i, j, k;
+  if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
+  const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
+  const double g0 = gu[e], g1 = gu[NE + e], g2 = gu[2 * NE + e];
+  if (g0 == 0.0 && g1 == 0.0 && g2 == 0.0) return;
+  Geo G;
+  load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+  const double xi[3] = {0.0, 0.0, 0.0};
+  double J[3][3], adj[3][3];
+  jacobian_at(G, xi, J);
+  const double inv = 1.0 / adjugate(J, adj);
+  const double v[3] = {g0 * d0, g1 * d1, g2 * d2};
+  double w[3];  // J^{-1} v
+#pragma unroll
+  for (int r = 0; r < 3; ++r) w[r] = (adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2]) * inv;
+  const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    double dN[3];
+    dshape(n, xi, dN);
+    const int64_t id = sidx(nx + 1, ny + 1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+    h[id] += dN[0] * w[0] + dN[1] * w[1] + dN[2] * w[2];
+    du0[id] += 0.125 * g0;
+    du0[N + id] += 0.125 * g1;
+    du0[2 * N + id] += 0.125 * g2;
+  }
+}
+
+// du0 -= I^T B^T mu per element class, and block partials of (E_0..2, T_0..2).
+__global__ void __launch_bounds__(128) k_adjoint_finish(int nx, int ny, int nz,
+                                                        const double* __restrict__ X,
+                                                        const double* __restrict__ Y,
+                                                        const double* __restrict__ Z,
+                                                        const double* __restrict__ mu,
+                                                        const double* __restrict__ lam,
+                                                        const double* __restrict__ gu,
+                                                        double* __restrict__ du0,
+                                                        double* __restrict__ partials, int cls) {
+  int i, j, k;
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (elem_of_thread(nx, ny, nz, cls, i, j, k)) {
+    Geo G;
+    load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+    double me[8], le[8];
+    int64_t id[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      id[n] = sidx(nx + 1, ny + 1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+      me[n] = mu[id[n]];
+      le[n] = lam[id[n]];
+    }
+    double out[8][3];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) out[n][0] = out[n][1] = out[n][2] = 0.0;
+#pragma unroll
+    for (int gp = 0; gp < 8; ++gp) {
+      double xi[3], J[3][3], adj[3][3];
+      gauss_xi(gp, xi);
+      jacobian_at(G, xi, J);
+      const double inv = 1.0 / adjugate(J, adj);
+      double dm[3] = {0.0, 0.0, 0.0}, dl[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        double dN[3];
+        dshape(n, xi, dN);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) { dm[r] += me[n] * dN[r]; dl[r] += le[n] * dN[r]; }
+      }
+      double gm[3], gl[3];  // detJ grad mu, detJ grad lambda (adj^T times the reference gradient)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        gm[d] = adj[0][d] * dm[0] + adj[1][d] * dm[1] + adj[2][d] * dm[2];
+        gl[d] = adj[0][d] * dl[0] + adj[1][d] * dl[1] + adj[2][d] * dl[2];
+        acc[d] += gm[d] * gl[d] * inv;
+      }
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const double Nn = shape(n, xi);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) out[n][d] -= Nn * gm[d];
+      }
+    }
+    const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
+    const double gc[3] = {gu[e], gu[NE + e], gu[2 * NE + e]};
+    if (gc[0] != 0.0 || gc[1] != 0.0 || gc[2] != 0.0) {
+      const double xi[3] = {0.0, 0.0, 0.0};
+      double J[3][3], adj[3][3], dl[3] = {0.0, 0.0, 0.0};
+      jacobian_at(G, xi, J);
+      const double inv = 1.0 / adjugate(J, adj);
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        double dN[3];
+        dshape(n, xi, dN);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) dl[r] += le[n] * dN[r];
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        acc[3 + d] += gc[d] * (adj[0][d] * dl[0] + adj[1][d] * dl[1] + adj[2][d] * dl[2]) * inv;
+    }
+    const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) du0[d * N + id[n]] += out[n][d];
+  }
+  __shared__ double red[6][4];
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((t & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[q][t >> 5] = acc[q];
+  __syncthreads();
+  if (t == 0) {
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) partials[blk * 6 + q] = red[q][0] + red[q][1] + red[q][2] + red[q][3];
+  }
+}
+
+// fixed-order sum of n six-component partials
+__global__ void __launch_bounds__(32) k_sum6(const double* __restrict__ p, int n, double* out) {
+  const int q = threadIdx.x;
+  if (q >= 6) return;
+  double s = 0.0;
+  for (int b = 0; b < n; ++b) s += p[(int64_t)b * 6 + q];
+  out[q] = s;
 }
 
 dim3 elem_grid(int nx, int ny, int nz, int cls, dim3 blk) {
@@ -478,18 +654,64 @@ cudaError_t launch_weak_div(int nx, int ny, int nz, const double* X, const doubl
   return cudaGetLastError();
 }
 
+int adjoint_partials(int nx, int ny, int nz) {
+  dim3 blk(32, 4, 1);
+  int total = 0;
+  for (int cls = 0; cls < 8; ++cls) {
+    dim3 grd = elem_grid(nx, ny, nz, cls, blk);
+    total += (int)(grd.x * grd.y * grd.z);
+  }
+  return total;
+}
+
+cudaError_t launch_recover_adjoint(int nx, int ny, int nz, const double* X, const double* Y,
+                                   const double* Z, const double* gu, const double* a, double* h,
+                                   double* du0, cudaStream_t st) {
+  dim3 blk(32, 4, 1);
+  for (int cls = 0; cls < 8; ++cls) {
+    dim3 grd = elem_grid(nx, ny, nz, cls, blk);
+    if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
+    k_recover_adjoint<<<grd, blk, 0, st>>>(nx, ny, nz, X, Y, Z, gu, 1.0 / (a[0] * a[0]),
+                                           1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), h, du0, cls);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_finish(int nx, int ny, int nz, const double* X, const double* Y,
+                                  const double* Z, const double* mu, const double* lam,
+                                  const double* gu, double* du0, double* partials, int cap,
+                                  double* sums6, cudaStream_t st) {
+  dim3 blk(32, 4, 1);
+  const int total = adjoint_partials(nx, ny, nz);
+  if (total > cap) return cudaErrorInvalidValue;
+  int off = 0;
+  for (int cls = 0; cls < 8; ++cls) {
+    dim3 grd = elem_grid(nx, ny, nz, cls, blk);
+    const int nb = (int)(grd.x * grd.y * grd.z);
+    if (nb == 0) continue;
+    k_adjoint_finish<<<grd, blk, 0, st>>>(nx, ny, nz, X, Y, Z, mu, lam, gu, du0,
+                                          partials + (int64_t)off * 6, cls);
+    count_launches(1);
+    off += nb;
+  }
+  k_sum6<<<1, 32, 0, st>>>(partials, off, sums6);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* X,
                            const double* Y, const double* Z, const double* u0,
-                           const double* lam, const double* a, int where, double* u,
-                           cudaStream_t st) {
+                           const double* lam, const double* a, int where, int u0_centers,
+                           double* u, cudaStream_t st) {
   dim3 blk(32, 4, 1);
   dim3 grd((nx + 31) / 32, (ny + 3) / 4, nz);
   if (where == 0)
     k_recover<1><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, lam, 1.0 / (a[0] * a[0]),
-                                      1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u);
+                                      1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u0_centers, u);
   else
     k_recover<8><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, lam, 1.0 / (a[0] * a[0]),
-                                      1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u);
+                                      1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u0_centers, u);
   count_launches(1);
   return cudaGetLastError();
 }

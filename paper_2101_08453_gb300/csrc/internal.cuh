@@ -126,6 +126,8 @@ struct mcwind_plan_s {
   int nx, ny, nz;
   double a[3];
   mcwind_options opt;
+  int gs_rows = 4;                          // smoother thread-block height (tunable)
+  bool in_batch = false;
   std::vector<mcw::Level> lv;
   // workspace layout (byte offsets) and sizes
   size_t ws_bytes = 0;
@@ -135,6 +137,8 @@ struct mcwind_plan_s {
   size_t off_scalars = 0;                   // device scalars / flags
   size_t off_cfree = 0;                     // coarsest free-node grid indices
   size_t off_cg = 0;                        // 6 finest-level float64 vectors of CG
+  size_t off_adj = 0;                       // adjoint reduction partials (6 per block) + sums
+  int n_adj = 0;
   int n_coarse = 0;
   int n_partials = 0;
   // bound at assemble
@@ -154,8 +158,9 @@ struct mcwind_plan_s {
   int prof_open = 0;
   double prof_ms[MCWIND_K_KINDS] = {0};
   long long prof_n[MCWIND_K_KINDS] = {0};
-  // per-plan CUDA objects
+  // per-plan CUDA objects: one solver iteration captured as a graph
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t cycle_graph[2] = {nullptr, nullptr};
-  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t iter_exec = nullptr;
+  const char* iter_ws = nullptr;     // workspace the graph was captured with
+  long long iter_launches = 0;       // kernels in one replay
 };

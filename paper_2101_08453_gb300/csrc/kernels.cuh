@@ -11,14 +11,28 @@ cudaError_t launch_assemble_stencil(const Grid& g, int nx, int ny, int nz, const
                                     const double* Y, const double* Z, const double* a,
                                     double* C, int* flag, cudaStream_t st);
 // Load vector (Eq. 5 right side) into f (split layout, zero on entry).
+// quad bit 0: one-point center rule; bit 1: u0 given at the element centers
+// ([3][nz][ny][nx]) instead of at the nodes.
 cudaError_t launch_assemble_rhs(const Grid& g, int nx, int ny, int nz, const double* X,
                                 const double* Y, const double* Z, const double* u0, int quad,
                                 double* f, cudaStream_t st);
 // u = u0 + A^{-1} grad lambda (Eq. 3); lambda in split layout.
 cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* X,
                            const double* Y, const double* Z, const double* u0,
-                           const double* lam, const double* a, int where, double* u,
-                           cudaStream_t st);
+                           const double* lam, const double* a, int where, int u0_centers,
+                           double* u, cudaStream_t st);
+// adjoint of the recovery at element centers: h += G^T A^{-1} gu, du0 += C^T gu
+// (standard layouts, zero on entry)
+cudaError_t launch_recover_adjoint(int nx, int ny, int nz, const double* X, const double* Y,
+                                   const double* Z, const double* gu, const double* a, double* h,
+                                   double* du0, cudaStream_t st);
+// du0 -= I^T B^T mu; sums6 = (E_0..2, T_0..2) over all elements (partials: 6 per
+// block, adjoint_partials(nx, ny, nz) blocks, refused above cap blocks)
+int adjoint_partials(int nx, int ny, int nz);
+cudaError_t launch_adjoint_finish(int nx, int ny, int nz, const double* X, const double* Y,
+                                  const double* Z, const double* mu, const double* lam,
+                                  const double* gu, double* du0, double* partials, int cap,
+                                  double* sums6, cudaStream_t st);
 // (B u)_m at every node, out in standard layout, zero on entry.
 cudaError_t launch_weak_div(int nx, int ny, int nz, const double* X, const double* Y,
                             const double* Z, const double* ug, double* out, cudaStream_t st);
@@ -44,9 +58,10 @@ cudaError_t launch_norm2_partials(const Grid& g, const double* v, double* partia
                                   int* nblocks, cudaStream_t st);
 
 // ---- smooth.cu: vertical Gauss-Seidel, one column group (Sec. 3) ----
+// rows: column rows per thread block (blockDim = 32 x rows, rows in 1..8)
 template <typename T>
 cudaError_t launch_gs_group(const Grid& g, const T* C, const T* f, T* x, int group, int up,
-                            cudaStream_t st);
+                            int rows, cudaStream_t st);
 
 // ---- transfer.cu ----
 // r = f - K x at free nodes (0 elsewhere); partials of sum r^2 if partials != nullptr
@@ -87,20 +102,20 @@ cudaError_t launch_dense_solve(const double* Ainv, int n, const int* cfree, cons
                                cudaStream_t st);
 
 // ---- krylov.cu: V-cycle-preconditioned conjugate gradients ----
-// device scalars s[0..4] = (r.z, r_prev.z, previous r.z, beta, p.Kp)
+// device scalars s[0..5] = (r.z, r_prev.z, previous r.z, beta, p.Kp, restart flag)
 int krylov_blocks(const Grid& g);
 template <typename TZ>
 cudaError_t launch_cg_dots(const Grid& g, const double* r, const double* rp, const TZ* z,
                            double* partials, int cap, double* s, cudaStream_t st);
 template <typename TZ>
-cudaError_t launch_cg_direction(const Grid& g, const TZ* z, double* p, double* s, int first,
+cudaError_t launch_cg_direction(const Grid& g, const TZ* z, double* p, double* s,
                                 cudaStream_t st);
 template <typename TP>
 cudaError_t launch_cg_update(const Grid& g, double* x, double* r, double* rp, const double* p,
                              const double* q, TP* pf, TP* px, double* s, double* partials,
                              int cap, double* rr_out, cudaStream_t st);
 template <typename TP>
-cudaError_t launch_cg_start(const Grid& g, const double* r, double* rp, TP* pf, TP* px,
+cudaError_t launch_cg_start(const Grid& g, const double* r, double* rp, TP* pf, TP* px, double* s,
                             cudaStream_t st);
 cudaError_t launch_reduce_pairs(const double* partials, int n, double* out0, double* out1,
                                 cudaStream_t st);

@@ -58,11 +58,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_dots(Grid g, const double* __re
   block_partial2(a, b, partials);
 }
 
-// s[0] = r.z, s[1] = rp.z, s[2] = previous r.z, s[3] = beta (written), s[4] = p.Kp
-__global__ void k_cg_beta(double* s, int first) {
+// s[0] = r.z, s[1] = rp.z, s[2] = previous r.z, s[3] = beta (written), s[4] = p.Kp,
+// s[5] = restart flag (set by k_cg_start, cleared here: beta = 0 after a restart)
+__global__ void k_cg_beta(double* s) {
   const double rz = s[0], rpz = s[1], old = s[2];
-  s[3] = first ? 0.0 : (rz - rpz) / old;
+  s[3] = s[5] != 0.0 ? 0.0 : (rz - rpz) / old;
   s[2] = rz;
+  s[5] = 0.0;
 }
 
 template <typename TZ>
@@ -112,7 +114,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, double* __restri
 template <typename TP>
 __global__ void __launch_bounds__(kThreads) k_cg_start(Grid g, const double* __restrict__ r,
                                                        double* __restrict__ rp,
-                                                       TP* __restrict__ pf, TP* __restrict__ px) {
+                                                       TP* __restrict__ pf, TP* __restrict__ px,
+                                                       double* __restrict__ s) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+      threadIdx.y == 0)
+    s[5] = 1.0;
   int64_t own;
   if (!free_column(g, own)) return;
   for (int k = 0; k <= g.Nz - 2; ++k) {
@@ -171,9 +177,9 @@ cudaError_t launch_cg_dots(const Grid& g, const double* r, const double* rp, con
 }
 
 template <typename TZ>
-cudaError_t launch_cg_direction(const Grid& g, const TZ* z, double* p, double* s, int first,
+cudaError_t launch_cg_direction(const Grid& g, const TZ* z, double* p, double* s,
                                 cudaStream_t st) {
-  k_cg_beta<<<1, 1, 0, st>>>(s, first); count_launches(1);
+  k_cg_beta<<<1, 1, 0, st>>>(s); count_launches(1);
   k_cg_direction<TZ><<<col_grid(g), dim3(32, 4), 0, st>>>(g, z, p, s); count_launches(1);
   return cudaGetLastError();
 }
@@ -191,9 +197,9 @@ cudaError_t launch_cg_update(const Grid& g, double* x, double* r, double* rp, co
 }
 
 template <typename TP>
-cudaError_t launch_cg_start(const Grid& g, const double* r, double* rp, TP* pf, TP* px,
+cudaError_t launch_cg_start(const Grid& g, const double* r, double* rp, TP* pf, TP* px, double* s,
                             cudaStream_t st) {
-  k_cg_start<TP><<<col_grid(g), dim3(32, 4), 0, st>>>(g, r, rp, pf, px); count_launches(1);
+  k_cg_start<TP><<<col_grid(g), dim3(32, 4), 0, st>>>(g, r, rp, pf, px, s); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -207,9 +213,9 @@ template cudaError_t launch_cg_dots<double>(const Grid&, const double*, const do
                                             const double*, double*, int, double*, cudaStream_t);
 template cudaError_t launch_cg_dots<float>(const Grid&, const double*, const double*,
                                            const float*, double*, int, double*, cudaStream_t);
-template cudaError_t launch_cg_direction<double>(const Grid&, const double*, double*, double*, int,
+template cudaError_t launch_cg_direction<double>(const Grid&, const double*, double*, double*,
                                                  cudaStream_t);
-template cudaError_t launch_cg_direction<float>(const Grid&, const float*, double*, double*, int,
+template cudaError_t launch_cg_direction<float>(const Grid&, const float*, double*, double*,
                                                 cudaStream_t);
 template cudaError_t launch_cg_update<double>(const Grid&, double*, double*, double*,
                                               const double*, const double*, double*, double*,
@@ -218,8 +224,8 @@ template cudaError_t launch_cg_update<float>(const Grid&, double*, double*, doub
                                              const double*, float*, float*, double*, double*, int,
                                              double*, cudaStream_t);
 template cudaError_t launch_cg_start<double>(const Grid&, const double*, double*, double*,
-                                             double*, cudaStream_t);
+                                             double*, double*, cudaStream_t);
 template cudaError_t launch_cg_start<float>(const Grid&, const double*, double*, float*, float*,
-                                            cudaStream_t);
+                                            double*, cudaStream_t);
 
 }  // namespace mcw

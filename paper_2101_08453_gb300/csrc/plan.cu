@@ -105,6 +105,8 @@ extern "C" void mcwind_default_options(mcwind_options* o) {
   o->rhs_quad = MCWIND_RHS_GAUSS8;
   o->post_reverse = 1;
   o->accel = MCWIND_ACCEL_NONE;
+  o->use_graphs = 1;
+  o->u0_at = MCWIND_U0_NODES;
 }
 
 extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], double h1,
@@ -134,6 +136,8 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   if (o.post_reverse != 0 && o.post_reverse != 1) return MCWIND_EINVAL;
   if (o.accel != MCWIND_ACCEL_NONE && o.accel != MCWIND_ACCEL_CG) return MCWIND_EINVAL;
   if (o.accel == MCWIND_ACCEL_CG && o.post_reverse != 1) return MCWIND_EINVAL;
+  if (o.use_graphs != 0 && o.use_graphs != 1) return MCWIND_EINVAL;
+  if (o.u0_at != MCWIND_U0_NODES && o.u0_at != MCWIND_U0_CENTERS) return MCWIND_EINVAL;
 
   std::vector<PlanLevel> H = hierarchy(nx, ny, nz, a, h1, h3, o.coarsen_rule, o.coarsest_max);
   if (H.empty() || !H.back().kmap.empty()) return MCWIND_EINVAL;
@@ -193,6 +197,9 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
     p->off_cg = off;
     off = align256(off + 6 * align256(t0 * 8));
   }
+  p->n_adj = adjoint_partials(nx, ny, nz);
+  p->off_adj = off;
+  off = align256(off + (6 * (size_t)p->n_adj + 8) * 8);
   p->n_partials = 2 * max_blocks;
   p->off_partials = off; off = align256(off + (size_t)p->n_partials * 8);
   p->off_scalars = off; off = align256(off + 256);

@@ -12,7 +12,7 @@ namespace mcw {
 namespace {
 
 template <typename T, bool UP>
-__global__ void __launch_bounds__(128) k_gs(Grid g, const T* __restrict__ C,
+__global__ void __launch_bounds__(256) k_gs(Grid g, const T* __restrict__ C,
                                             const T* __restrict__ f, T* __restrict__ x, int pi,
                                             int pj) {
   const int ih = blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,10 +94,10 @@ __global__ void __launch_bounds__(128) k_gs(Grid g, const T* __restrict__ C,
 
 template <typename T>
 cudaError_t launch_gs_group(const Grid& g, const T* C, const T* f, T* x, int group, int up,
-                            cudaStream_t st) {
+                            int rows, cudaStream_t st) {
   const int pi = group & 1, pj = group >> 1;
-  dim3 blk(32, 4);
-  dim3 grd(((g.Nx + 1) / 2 + 31) / 32, ((g.Ny + 1) / 2 + 3) / 4);
+  dim3 blk(32, rows);
+  dim3 grd(((g.Nx + 1) / 2 + 31) / 32, ((g.Ny + 1) / 2 + rows - 1) / rows);
   if (up)
     k_gs<T, true><<<grd, blk, 0, st>>>(g, C, f, x, pi, pj);
   else
@@ -107,8 +107,8 @@ cudaError_t launch_gs_group(const Grid& g, const T* C, const T* f, T* x, int gro
 }
 
 template cudaError_t launch_gs_group<double>(const Grid&, const double*, const double*, double*,
-                                             int, int, cudaStream_t);
+                                             int, int, int, cudaStream_t);
 template cudaError_t launch_gs_group<float>(const Grid&, const float*, const float*, float*, int,
-                                            int, cudaStream_t);
+                                            int, int, cudaStream_t);
 
 }  // namespace mcw

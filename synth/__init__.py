@@ -245,6 +245,33 @@ def full_domain_window(i0, j0, w, h, nx=3000, ny=3000, nz=15, seed=0, a=(1.0, 1.
                 np.ascontiguousarray(Z), u0, dx, layer_thicknesses(nz), {"theta": theta})
 
 
+def batch_domains(n=96, seed=0, nmin=48, nmax=384, zmin=8, zmax=20, a3_choices=(1.0, 4.0, 10.0),
+                  dx=DX):
+    """n independent domains of uneven sizes: horizontal cells uniform in
+    [nmin, nmax] per axis, vertical cells uniform in [zmin, zmax], a3 drawn
+    from a3_choices (a1 = a2 = 1); each with a few random hills (H ~ U[50,150]
+    m, sigma ~ U[200,600] m, one per 100 x 100 cells, at least one) and a
+    log-law wind of 8 m/s from a random direction plus N(0, 0.2) per node."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for d in range(n):
+        nx = int(rng.integers(nmin, nmax + 1))
+        ny = int(rng.integers(nmin, nmax + 1))
+        nz = int(rng.integers(zmin, zmax + 1))
+        a3 = float(a3_choices[int(rng.integers(0, len(a3_choices)))])
+        x = dx * np.arange(nx + 1)
+        y = dx * np.arange(ny + 1)
+        zs = np.zeros((ny + 1, nx + 1))
+        for _ in range(max(1, (nx * ny) // 10000)):
+            add_hill(zs, x, y, rng.uniform(0, x[-1]), rng.uniform(0, y[-1]),
+                     rng.uniform(50.0, 150.0), rng.uniform(200.0, 600.0))
+        X, Y, Z, zeta = node_grid(nx, ny, nz, zs, dx)
+        u0 = log_wind(nx, ny, nz, zeta, 8.0, rng.uniform(0.0, 360.0), 0.2, rng)
+        out.append(Case(f"dom{d}_{nx}x{ny}x{nz}_a{a3:g}", nx, ny, nz, (1.0, 1.0, a3), X, Y, Z, u0,
+                        dx, layer_thicknesses(nz)))
+    return out
+
+
 def perturb_wind(u0: np.ndarray, seed: int, rel: float = 0.02) -> np.ndarray:
     """The next time step's first guess: u0 * (1 + rel * xi), xi ~ N(0, 1)."""
     rng = np.random.default_rng(seed + 1000003)

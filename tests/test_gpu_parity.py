@@ -330,3 +330,44 @@ def test_cg_warm_start(torch):
     lam_c, st_c = plan.solve(u0b, rtol=1e-10)
     assert st_warm.status == m.MCWIND_OK and st_warm.cycles < st_c.cycles
     assert rel(lam_w.cpu().numpy(), lam_c.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("accel", [m.ACCEL_NONE, m.ACCEL_CG])
+@pytest.mark.parametrize("precision", [m.PREC_F64, m.PREC_MIXED])
+def test_graph_replay_matches_direct_launches(torch, accel, precision):
+    """Replaying the captured iteration graph gives bitwise the same solution
+    and history as launching the same kernels directly."""
+    _, pg, (X, Y, Z, u0), _ = setup(torch, "ragged", precision=precision, coarsest_max=1024,
+                                    accel=accel, use_graphs=1)
+    _, pd, _, _ = setup(torch, "ragged", precision=precision, coarsest_max=1024, accel=accel,
+                        use_graphs=0)
+    n0 = m.lib().mcwind_launch_count()
+    a, sa = pg.solve(u0, rtol=1e-10, max_cycles=60)
+    n1 = m.lib().mcwind_launch_count()
+    b, sb = pd.solve(u0, rtol=1e-10, max_cycles=60)
+    n2 = m.lib().mcwind_launch_count()
+    assert sa.cycles == sb.cycles and sa.history() == sb.history()
+    assert torch.equal(a, b)
+    assert n1 - n0 == n2 - n1   # replayed kernels are counted too
+
+
+@pytest.mark.parametrize("quad", [m.RHS_GAUSS8, m.RHS_CENTER1])
+def test_wind_at_centers(torch, quad):
+    """u0 given at the element centers: load vector, solution and recovered
+    wind against the oracle's center-wind routines."""
+    c = CASES["ragged"]
+    rng = np.random.default_rng(4)
+    uc = rng.normal(size=(3, c.nz, c.ny, c.nx)) + np.array([5.0, -2.0, 0.0])[:, None, None, None]
+    X, Y, Z, ucd = to_dev(torch, c.X, c.Y, c.Z, uc)
+    plan = m.Plan.for_case(c, rhs_quad=quad, u0_at=m.U0_CENTERS, precision=m.PREC_MIXED)
+    plan.assemble(X, Y, Z)
+    free = oracle.case_free_mask(c)
+    f_ref = np.where(free, oracle.assemble_f_centers(c, uc, quad), 0.0)
+    f = plan.rhs(ucd).cpu().numpy().ravel()
+    assert np.abs(f - f_ref).max() <= 1e-12 * np.abs(f_ref).max()
+    lam, st = plan.solve(ucd, rtol=1e-12, max_cycles=120)
+    assert st.status == m.MCWIND_OK
+    lam_ref = oracle.solve(c, f=oracle.assemble_f_centers(c, uc, quad))
+    assert rel(lam.cpu().numpy().ravel(), lam_ref) <= 1e-10
+    u = plan.recover(ucd, lam).cpu().numpy()
+    assert rel(u, oracle.recover_centers(c, lam_ref, uc)) <= 1e-10

@@ -56,6 +56,7 @@ def test_plan_rejects_bad_sizes(args):
     dict(opt=dict(coarsest_max=0)), dict(opt=dict(coarsest_max=100000)),
     dict(opt=dict(coarsen_rule=7)), dict(opt=dict(rhs_quad=2)),
     dict(opt=dict(accel=2)), dict(opt=dict(accel=1, post_reverse=0)),
+    dict(opt=dict(use_graphs=2)),
 ])
 def test_plan_rejects_bad_options(bad):
     a = bad.get("a", (1, 1, 1))
@@ -123,3 +124,26 @@ def test_full_domain_hierarchy_shape():
     last = plan.level(plan.num_levels - 1)
     assert (last["Nx"] - 2) * (last["Ny"] - 2) * (last["Nz"] - 1) <= 1024
     assert plan.workspace_bytes < 150e9
+
+
+def test_batch_rejects_bad_arguments_without_gpu():
+    import ctypes
+    L = m.lib()
+    assert L.mcwind_batch_workspace_bytes(0) == 0
+    assert L.mcwind_batch_workspace_bytes(96) >= 96 * 16
+    h, _ = m.mcwind_plan_create(8, 8, 3, (1, 1, 1), 30.0, [5.0, 6.0, 7.0])
+    hc, _ = m.mcwind_plan_create(8, 8, 3, (1, 1, 1), 30.0, [5.0, 6.0, 7.0], m.default_options(accel=1))
+    try:
+        out = ctypes.c_void_p()
+        ws = ctypes.c_void_p(256)
+        two = (ctypes.c_void_p * 2)(h, h)
+        assert L.mcwind_batch_create(2, two, ws, ctypes.byref(out)) == m.MCWIND_EINVAL
+        one = (ctypes.c_void_p * 1)(hc)
+        assert L.mcwind_batch_create(1, one, ws, ctypes.byref(out)) == m.MCWIND_EINVAL
+        assert L.mcwind_batch_create(0, one, ws, ctypes.byref(out)) == m.MCWIND_EINVAL
+        assert L.mcwind_plan_set_tuning(h, 0, 0, 4) == m.MCWIND_EINVAL
+        assert L.mcwind_plan_set_tuning(h, 2, 2, 3) == m.MCWIND_EINVAL
+        assert L.mcwind_plan_set_tuning(h, 3, 3, 8) == m.MCWIND_OK
+    finally:
+        m.mcwind_plan_destroy(h)
+        m.mcwind_plan_destroy(hc)

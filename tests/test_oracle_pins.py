@@ -356,3 +356,49 @@ def test_vcycle_is_symmetric_operator():
     b1 = H.vcycle(0, f1, np.zeros_like(f1))
     b2 = H.vcycle(0, f2, np.zeros_like(f2))
     assert abs(f2 @ b1 - f1 @ b2) <= 1e-12 * abs(f2 @ b1)
+
+
+def test_dense_wind_gradient_against_finite_differences():
+    """The probed-Jacobian gradient agrees with central differences of the
+    oracle's forward map, and the log-a derivatives sum to zero (a -> c a
+    leaves u unchanged, Sec. 2 / P8)."""
+    c = synth.single_hill(5, 4, 3, sigma=40.0, height=20.0, noise=0.5, a=(1.0, 1.3, 2.0))
+    rng = np.random.default_rng(0)
+    gu = rng.normal(size=(3, c.nz, c.ny, c.nx))
+    g0, gl = oracle.dense_wind_gradient(c, gu)
+
+    def loss(u0):
+        lam = oracle.solve(c, u0=u0)
+        return float(gu.ravel() @ oracle.recover(c, lam, u0=u0).ravel())
+
+    for idx in [(0, 0, 0, 0), (1, 2, 2, 3), (2, 3, 4, 5), (0, 1, 3, 1)]:
+        up, um = c.u0.copy(), c.u0.copy()
+        up[idx] += 1e-6
+        um[idx] -= 1e-6
+        fd = (loss(up) - loss(um)) / 2e-6
+        assert fd == pytest.approx(g0[idx], rel=1e-6, abs=1e-8)
+    assert abs(sum(gl)) <= 1e-6 * max(abs(v) for v in gl)
+
+
+def test_center_wind_load_vector():
+    """A wind given at the element centers (Sec. 2's representation) that is
+    constant gives the same load vector as the same constant at the nodes;
+    a center wind that varies gives the nodal result of its mean per element
+    for the one-point rule."""
+    c = synth.jittered(5, 4, 3, seed=8)
+    uc = np.zeros((3, c.nz, c.ny, c.nx))
+    uc[0], uc[1], uc[2] = 1.5, -0.7, 0.3
+    c.u0[0], c.u0[1], c.u0[2] = 1.5, -0.7, 0.3
+    for quad in (0, 1):
+        a = oracle.assemble_f_centers(c, uc, quad)
+        b = oracle.assemble_f(c, quad=quad)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    rng = np.random.default_rng(2)
+    u0 = rng.normal(size=c.u0.shape)
+    mean = np.zeros_like(uc)
+    for n in range(8):
+        mean += u0[:, (n >> 2) & 1: c.nz + ((n >> 2) & 1), (n >> 1) & 1: c.ny + ((n >> 1) & 1),
+                   n & 1: c.nx + (n & 1)] / 8.0
+    a = oracle.assemble_f_centers(c, mean, 1)
+    b = oracle.assemble_f(c, u0=u0, quad=1)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
