@@ -288,10 +288,11 @@ size_t mcwind_batch_workspace_bytes(int n);
 int mcwind_batch_create(int n, const mcwind_plan* plans, void* workspace, mcwind_batch* out);
 
 /* Solve every domain d: u0[d], lambda[d] as in mcwind_solve.  Iterates until
- * every domain is at or below rtol or max_cycles; domains that converge first
- * keep iterating (their residual only decreases) and stats[d].cycles records
- * the cycle at which domain d first reached rtol.  stats: host, n entries, may
- * be NULL.  Returns OK, ENOTCONV (some domain above rtol), ENONFINITE, EINVAL. */
+ * every domain is at or below rtol or max_cycles; a domain stops iterating
+ * once it reaches rtol (one cached graph per set of still-active domains), so
+ * each domain gets exactly the result of its own mcwind_solve.  stats: host,
+ * n entries, may be NULL.  Returns OK, ENOTCONV (some domain above rtol),
+ * ENONFINITE, EINVAL. */
 int mcwind_batch_solve(mcwind_batch batch, const double* const* u0, double* const* lambda,
                        double rtol, int max_cycles, unsigned flags, mcwind_stats* stats,
                        void* stream);

@@ -1,6 +1,8 @@
 // C entry points and the solve driver.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <string>
 
 #include "kernels.cuh"
 
@@ -820,10 +822,10 @@ struct mcwind_batch_s {
   cudaStream_t cap = nullptr;
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> joins;
-  cudaGraphExec_t exec = nullptr;
+  // one iteration graph per set of still-active domains (key: '0'/'1' per domain)
+  std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;
   std::vector<const char*> ws_at_capture;
   std::vector<long long> tuning_at_capture;
-  long long launches = 0;
 };
 
 namespace {
@@ -832,11 +834,13 @@ long long tuning_key(mcwind_plan p) {
   return ((long long)p->opt.nu_pre << 16) | ((long long)p->opt.nu_post << 8) | p->gs_rows;
 }
 
-// fork the batch's domain streams off st, run body(d) on each, join back into st
+// fork the batch's domain streams off st, run body(d) on the selected
+// domains, join back into st
 template <typename Body>
-int fork_join(mcwind_batch b, cudaStream_t st, Body body) {
+int fork_join(mcwind_batch b, cudaStream_t st, const std::string& active, Body body) {
   CK(cudaEventRecord(b->fork, st));
   for (size_t d = 0; d < b->plans.size(); ++d) {
+    if (active[d] != '1') continue;
     CK(cudaStreamWaitEvent(b->streams[d], b->fork, 0));
     CKR(body((int)d, b->streams[d]));
     CK(cudaEventRecord(b->joins[d], b->streams[d]));
@@ -845,24 +849,33 @@ int fork_join(mcwind_batch b, cudaStream_t st, Body body) {
   return MCWIND_OK;
 }
 
-int batch_iteration_body(mcwind_batch b, cudaStream_t st) {
-  return fork_join(b, st, [b](int d, cudaStream_t s) -> int {
-    mcwind_plan p = b->plans[d];
-    CKR(one_cycle(p, s));
-    CK(cudaMemcpyAsync(b->dres + 2 * d + 1, scal(p) + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
-    return (int)MCWIND_OK;
-  });
+void batch_clear_graphs(mcwind_batch b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.first);
+  b->graphs.clear();
 }
 
-int batch_iteration(mcwind_batch b, cudaStream_t st) {
-  bool stale = !b->exec;
+// one iteration of the active domains, from the graph cached for that set
+int batch_iteration(mcwind_batch b, const std::string& active, cudaStream_t st) {
+  bool stale = false;
   for (size_t d = 0; d < b->plans.size() && !stale; ++d)
     stale = b->ws_at_capture[d] != b->plans[d]->ws || b->tuning_at_capture[d] != tuning_key(b->plans[d]);
   if (stale) {
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    batch_clear_graphs(b);
+    for (size_t d = 0; d < b->plans.size(); ++d) {
+      b->ws_at_capture[d] = b->plans[d]->ws;
+      b->tuning_at_capture[d] = tuning_key(b->plans[d]);
+    }
+  }
+  auto it = b->graphs.find(active);
+  if (it == b->graphs.end()) {
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     const long long n0 = mcwind_launch_count();
-    const int rc = batch_iteration_body(b, b->cap);
+    const int rc = fork_join(b, b->cap, active, [b](int d, cudaStream_t s) -> int {
+      mcwind_plan p = b->plans[d];
+      CKR(one_cycle(p, s));
+      CK(cudaMemcpyAsync(b->dres + 2 * d + 1, scal(p) + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      return MCWIND_OK;
+    });
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (rc != MCWIND_OK) {
@@ -870,18 +883,16 @@ int batch_iteration(mcwind_batch b, cudaStream_t st) {
       return rc;
     }
     CK(e);
-    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     CK(ei);
-    b->launches = mcwind_launch_count() - n0;
-    count_launches(-(int)b->launches);
-    for (size_t d = 0; d < b->plans.size(); ++d) {
-      b->ws_at_capture[d] = b->plans[d]->ws;
-      b->tuning_at_capture[d] = tuning_key(b->plans[d]);
-    }
+    const long long nl = mcwind_launch_count() - n0;
+    count_launches(-(int)nl);
+    it = b->graphs.emplace(active, std::make_pair(exec, nl)).first;
   }
-  CK(cudaGraphLaunch(b->exec, st));
-  count_launches((int)b->launches);
+  CK(cudaGraphLaunch(it->second.first, st));
+  count_launches((int)it->second.second);
   return MCWIND_OK;
 }
 
@@ -930,7 +941,7 @@ extern "C" int mcwind_batch_create(int n, const mcwind_plan* plans, void* worksp
 
 extern "C" void mcwind_batch_destroy(mcwind_batch b) {
   if (!b) return;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
+  batch_clear_graphs(b);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -952,8 +963,9 @@ extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, doubl
     if (b->plans[d]->prof) return MCWIND_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const std::string all(n, '1');
   // per domain: load vector, its norm, first iterate, first residual
-  CKR(fork_join(b, st, [&](int d, cudaStream_t s) -> int {
+  CKR(fork_join(b, st, all, [&](int d, cudaStream_t s) -> int {
     mcwind_plan p = b->plans[d];
     Level& L0 = p->lv[0];
     Ptr64 A = lv64(p, 0);
@@ -990,8 +1002,10 @@ extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, doubl
     return status;
   }
   int c = 0;
+  std::string active(n, '0');
+  for (int d = 0; d < n; ++d) active[d] = S[d].cycles < 0 ? '1' : '0';
   while (!all_done && c < max_cycles) {
-    CKR(batch_iteration(b, st));
+    CKR(batch_iteration(b, active, st));
     CK(cudaMemcpyAsync(h.data(), b->dres, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     ++c;
@@ -999,8 +1013,12 @@ extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, doubl
     for (int d = 0; d < n; ++d) {
       if (S[d].cycles >= 0) continue;
       S[d].res_hist[c] = nf[d] > 0.0 ? std::sqrt(h[2 * d + 1]) / nf[d] : 0.0;
-      if (S[d].res_hist[c] <= rtol || !std::isfinite(S[d].res_hist[c])) S[d].cycles = c;
-      else all_done = false;
+      if (S[d].res_hist[c] <= rtol || !std::isfinite(S[d].res_hist[c])) {
+        S[d].cycles = c;
+        active[d] = '0';
+      } else {
+        all_done = false;
+      }
     }
   }
   for (int d = 0; d < n; ++d) {
@@ -1014,7 +1032,7 @@ extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, doubl
     T.status = T.rel_res <= rtol ? MCWIND_OK : MCWIND_ENOTCONV;
     if (T.status != MCWIND_OK) status = MCWIND_ENOTCONV;
   }
-  CKR(fork_join(b, st, [&](int d, cudaStream_t s) -> int {
+  CKR(fork_join(b, st, all, [&](int d, cudaStream_t s) -> int {
     mcwind_plan p = b->plans[d];
     CK(launch_split_to_std<double>(p->lv[0].g, lv64(p, 0).x, lambda[d], s));
     return (int)MCWIND_OK;
