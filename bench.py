@@ -438,6 +438,15 @@ def main():
         work_all = float(work)
     value = work_all / t_dev
 
+    # one more step without the profiler (solver iterations replayed from graphs)
+    u0e, u1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    u0e.record()
+    step()
+    u1e.record()
+    barrier()
+    ms_unprofiled = u0e.elapsed_time(u1e)
+
     # ---- end to end through the public API with host buffers ------------
     e2e = None
     if not args.no_e2e:
@@ -602,6 +611,7 @@ def main():
         "time_to_1e-8": tt,
         "vcycle_rate": {k: n_free * v["cold_cycles"] / v["cold_s"] for k, v in tt.items()},
         "wall_s": wall,
+        "ms_per_step_unprofiled_graphs": ms_unprofiled,
         "roofline": dom_roof,
         "roofline_kernels": roof_kernels,
         "roofline_kernels_f64_solve": roof_f64,

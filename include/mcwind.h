@@ -71,6 +71,7 @@ enum { MCWIND_AT_CENTERS = 0, MCWIND_AT_GAUSS = 1 };
 enum { MCWIND_FORWARD = 0, MCWIND_BACKWARD = 1 };
 enum { MCWIND_ACCEL_NONE = 0, MCWIND_ACCEL_CG = 1 };
 enum { MCWIND_U0_NODES = 0, MCWIND_U0_CENTERS = 1 };
+enum { MCWIND_ARITH_F64 = 0, MCWIND_ARITH_DFLOAT = 1 };
 
 #define MCWIND_WARM 1u        /* mcwind_solve flag: start from the caller's lambda */
 #define MCWIND_HIST 256
@@ -115,6 +116,12 @@ typedef struct {
      constant over the element in the load vector and in the recovery.  The
      gradient entry points require MCWIND_U0_NODES. */
   int u0_at;
+  /* Arithmetic of the 2x2x2-Gauss element kernels (stiffness and load
+     vector).  MCWIND_ARITH_DFLOAT (default): pairs of floats (about 48
+     significant bits) on the float pipe, which issues 61 times the float64
+     rate on GB300; MCWIND_ARITH_F64: float64.  Sums into the stencil and the
+     load vector, and everything after assembly, are float64 either way. */
+  int element_arith;
 } mcwind_options;
 
 typedef struct {

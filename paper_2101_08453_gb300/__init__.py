@@ -30,6 +30,7 @@ AT_CENTERS, AT_GAUSS = 0, 1
 FORWARD, BACKWARD = 0, 1
 ACCEL_NONE, ACCEL_CG = 0, 1
 U0_NODES, U0_CENTERS = 0, 1
+ARITH_F64, ARITH_DFLOAT = 0, 1
 WARM = 1
 HIST = 256
 
@@ -48,7 +49,8 @@ class Options(ctypes.Structure):
                 ("coarsen_rule", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("precision", ctypes.c_int), ("rhs_quad", ctypes.c_int),
                 ("post_reverse", ctypes.c_int), ("accel", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("u0_at", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("u0_at", ctypes.c_int),
+                ("element_arith", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -32,6 +32,24 @@ long long launches_now() { return mcwind_launch_count(); }
 // quadrature and u0 location of the load vector, as the element kernel takes them
 int rhs_mode(mcwind_plan p) { return (p->opt.rhs_quad & 1) | (p->opt.u0_at ? 2 : 0); }
 
+bool dfloat_elements(mcwind_plan p) { return p->opt.element_arith == MCWIND_ARITH_DFLOAT; }
+size_t std_nodes(mcwind_plan p) { return (size_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1); }
+
+// f (split layout, level 0) = load vector of Eq. 5 from u0
+cudaError_t rhs_into(mcwind_plan p, const double* u0, double* f, cudaStream_t st) {
+  const Level& L0 = p->lv[0];
+  const float2* xyz2 = (const float2*)(p->ws + p->off_xyz2);
+  float2* u2 = (float2*)(p->ws + p->off_u2);
+  const bool df = dfloat_elements(p);
+  cudaError_t e = cudaMemsetAsync(f, 0, sizeof(double) * (size_t)L0.g.total, st);
+  if (e == cudaSuccess && df && p->opt.u0_at == MCWIND_U0_NODES && (p->opt.rhs_quad & 1) == 0)
+    e = launch_split_pairs(u0, u2, 3 * (int64_t)std_nodes(p), st);
+  if (e == cudaSuccess)
+    e = launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, xyz2, u0, u2,
+                            rhs_mode(p), f, df, st);
+  return e;
+}
+
 // Records a CUDA event pair around a kernel class while profiling is on.
 // A scope reserves its two events when it opens; finished pairs are folded
 // into the per-class totals whenever the stream is idle, and the event pool
@@ -305,7 +323,15 @@ extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, 
   Level& L0 = p->lv[0];
   {
     PROF(MCWIND_K_ASSEMBLE);
-    CK(launch_assemble_stencil(L0.g, p->nx, p->ny, p->nz, X, Y, Z, p->a, at(p, L0.C64), flagp(p), st));
+    float2* xyz2 = (float2*)(p->ws + p->off_xyz2);
+    const int64_t nn = (int64_t)std_nodes(p);
+    if (dfloat_elements(p)) {
+      CK(launch_split_pairs(X, xyz2, nn, st));
+      CK(launch_split_pairs(Y, xyz2 + nn, nn, st));
+      CK(launch_split_pairs(Z, xyz2 + 2 * nn, nn, st));
+    }
+    CK(launch_assemble_stencil(L0.g, p->nx, p->ny, p->nz, X, Y, Z, xyz2, p->a, at(p, L0.C64),
+                               flagp(p), dfloat_elements(p), st));
   }
   {
     PROF(MCWIND_K_SETUP);
@@ -361,8 +387,8 @@ extern "C" int mcwind_rhs(mcwind_plan p, const double* u0, double* f, void* stre
   cudaStream_t st = (cudaStream_t)stream;
   Level& L0 = p->lv[0];
   Ptr64 A = lv64(p, 0);
-  CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, st));
-  CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, rhs_mode(p), A.f, st));
+  PROF(MCWIND_K_RHS);
+  CK(rhs_into(p, u0, A.f, st));
   CK(launch_split_to_std<double>(L0.g, A.f, f, st));
   return MCWIND_OK;
 }
@@ -439,8 +465,7 @@ int solve_cg(mcwind_plan p, const double* u0, const double* f_given, double* lam
     CK(launch_std_to_split<double>(L0.g, f_given, v.f, true, st));
   } else {
     PROF(MCWIND_K_RHS);
-    CK(cudaMemsetAsync(v.f, 0, sizeof(double) * (size_t)L0.g.total, st));
-    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, rhs_mode(p), v.f, st));
+    CK(rhs_into(p, u0, v.f, st));
   }
   CKR(norm2(p, L0.g, v.f, 0, st));
   {
@@ -529,8 +554,7 @@ static int solve_impl(mcwind_plan p, const double* u0, const double* f_given, do
     CK(launch_std_to_split<double>(L0.g, f_given, A.f, true, st));
   } else {
     PROF(MCWIND_K_RHS);
-    CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, st));
-    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0, rhs_mode(p), A.f, st));
+    CK(rhs_into(p, u0, A.f, st));
   }
   CKR(norm2(p, L0.g, A.f, 0, st));
   {
@@ -969,8 +993,7 @@ extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, doubl
     mcwind_plan p = b->plans[d];
     Level& L0 = p->lv[0];
     Ptr64 A = lv64(p, 0);
-    CK(cudaMemsetAsync(A.f, 0, sizeof(double) * (size_t)L0.g.total, s));
-    CK(launch_assemble_rhs(L0.g, p->nx, p->ny, p->nz, p->X, p->Y, p->Z, u0[d], rhs_mode(p), A.f, s));
+    CK(rhs_into(p, u0[d], A.f, s));
     CKR(norm2(p, L0.g, A.f, 0, s));
     if (flags & MCWIND_WARM)
       CK(launch_std_to_split<double>(L0.g, lambda[d], A.x, true, s));

@@ -32,13 +32,12 @@ __device__ __forceinline__ dflt df_of(double x) {
 __device__ __forceinline__ dflt df_of(float x) { return {x, 0.0f}; }
 __device__ __forceinline__ double to_double(dflt a) { return (double)a.hi + (double)a.lo; }
 
+// Sum with error at most about 2^-48 (|a| + |b|): the high parts are added
+// exactly (two-sum), the low parts in float, then renormalized.
 __device__ __forceinline__ dflt operator+(dflt a, dflt b) {
-  float s, e, t, f;
+  float s, e;
   two_sum(a.hi, b.hi, s, e);
-  two_sum(a.lo, b.lo, t, f);
-  e += t;
-  fast_two_sum(s, e, s, e);
-  e += f;
+  e += a.lo + b.lo;
   fast_two_sum(s, e, s, e);
   return {s, e};
 }

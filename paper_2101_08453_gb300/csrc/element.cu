@@ -23,6 +23,7 @@
 // Assembly scatters element contributions in 8 launches, one per element
 // parity class (i mod 2, j mod 2, k mod 2): elements of one class share no
 // node, so there are no atomics and the sums are deterministic.
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace mcw {
@@ -30,9 +31,11 @@ namespace {
 
 constexpr double kGp = 0.57735026918962576451;  // 1/sqrt(3), the 2-point Gauss abscissa
 
-struct Geo {
-  double e[3][4][3];  // e[r][q][d]: edge vectors parallel to reference axis r
+template <typename R>
+struct GeoT {
+  R e[3][4][3];  // e[r][q][d]: edge vectors parallel to reference axis r
 };
+using Geo = GeoT<double>;
 
 __device__ __forceinline__ int64_t sidx(int nx1, int ny1, int i, int j, int k) {
   return ((int64_t)k * ny1 + j) * nx1 + i;
@@ -57,6 +60,22 @@ __device__ __forceinline__ void load_geo(const double* X, const double* Y, const
     int nx0 = 0 + 2 * q1 + 4 * q2;   // axis 0 edge: b = q1, c = q2
     int ny0 = q1 + 0 + 4 * q2;       // axis 1 edge: a = q1, c = q2
     int nz0 = q1 + 2 * q2 + 0;       // axis 2 edge: a = q1, b = q2
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      G.e[0][q][d] = xe[nx0 + 1][d] - xe[nx0][d];
+      G.e[1][q][d] = xe[ny0 + 2][d] - xe[ny0][d];
+      G.e[2][q][d] = xe[nz0 + 4][d] - xe[nz0][d];
+    }
+  }
+}
+
+// Edge vectors from the 8 corner positions xe[n][d] (any arithmetic type).
+template <typename R>
+__device__ __forceinline__ void edges_of(const R xe[8][3], GeoT<R>& G) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int q1 = q & 1, q2 = q >> 1;
+    const int nx0 = 2 * q1 + 4 * q2, ny0 = q1 + 4 * q2, nz0 = q1 + 2 * q2;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       G.e[0][q][d] = xe[nx0 + 1][d] - xe[nx0][d];
@@ -137,6 +156,115 @@ __host__ __device__ constexpr double spow(int e) {
   return e == 0 ? 1.0 : (e == 1 ? kGp : (e == 2 ? kGp * kGp : (e == 3 ? kGp * kGp * kGp : kGp * kGp * kGp * kGp)));
 }
 
+// Element arithmetic in type R: double (the FP64 pipe) or dflt (float pairs
+// on the FP32 pipe, about 48 significant bits).
+template <typename R>
+struct Num;
+template <>
+struct Num<double> {
+  __device__ static double from(double v) { return v; }
+  __device__ static double to(double v) { return v; }
+  __device__ static double rcp(double v) { return 1.0 / v; }
+  __device__ static bool pos(double v) { return v > 0.0; }
+};
+template <>
+struct Num<dflt> {
+  __device__ static dflt from(double v) { return df_of(v); }
+  __device__ static double to(dflt v) { return to_double(v); }
+  __device__ static dflt rcp(dflt v) { return reciprocal(v); }
+  __device__ static bool pos(dflt v) { return positive(v); }
+};
+
+// Jacobian columns of the trilinear map at the 2-point Gauss abscissae:
+// column r at sign combination q (bit 0: first other axis positive, bit 1:
+// second) is 1/8 (S + s sig1 D1 + s sig2 D2 + s^2 sig1 sig2 D12), with S, D1,
+// D2, D12 the sum and signed sums of the 4 edges parallel to axis r.
+template <typename R>
+__device__ __forceinline__ void jac_columns(const GeoT<R>& G, R Jc[3][4][3]) {
+  const R cs = Num<R>::from(0.125 * kGp), cs2 = Num<R>::from(0.125 * kGp * kGp);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R e0 = G.e[r][0][d], e1 = G.e[r][1][d];
+      const R e2 = G.e[r][2][d], e3 = G.e[r][3][d];
+      const R p0 = e0 + e1, p1 = e2 + e3, m0 = e1 - e0, m1 = e3 - e2;
+      const R A = (p0 + p1) * 0.125f, B1 = (m0 + m1) * cs, B2 = (p1 - p0) * cs;
+      const R B12 = (m1 - m0) * cs2;
+      const R ApB = A + B12, AmB = A - B12, P = B1 + B2, M = B1 - B2;
+      Jc[r][3][d] = ApB + P;
+      Jc[r][0][d] = ApB - P;
+      Jc[r][1][d] = AmB + M;
+      Jc[r][2][d] = AmB - M;
+    }
+}
+
+// Element geometry in arithmetic R: float64 from X, Y, Z; float pairs from the
+// pre-split copy xyz2 ([3][nodes] of (hi, lo)).
+template <typename R>
+__device__ __forceinline__ void load_geo_t(const double* X, const double* Y, const double* Z,
+                                           const float2* xyz2, int64_t N, int nx1, int ny1, int i,
+                                           int j, int k, GeoT<R>& G) {
+  R xe[8][3];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int64_t id = sidx(nx1, ny1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+    if constexpr (sizeof(R) == sizeof(double) && !__is_same(R, dflt)) {
+      xe[n][0] = X[id];
+      xe[n][1] = Y[id];
+      xe[n][2] = Z[id];
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float2 v = xyz2[d * N + id];
+        xe[n][d] = R{v.x, v.y};
+      }
+    }
+  }
+  edges_of<R>(xe, G);
+}
+
+// J[d][r] at Gauss point gp from the columns
+template <typename R>
+__device__ __forceinline__ void jac_at_gauss(const R Jc[3][4][3], int gp, R J[3][3]) {
+  const int gx = gp & 1, gy = (gp >> 1) & 1, gz = (gp >> 2) & 1;
+  const int q0 = gy + 2 * gz, q1 = gx + 2 * gz, q2 = gx + 2 * gy;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    J[d][0] = Jc[0][q0][d];
+    J[d][1] = Jc[1][q1][d];
+    J[d][2] = Jc[2][q2][d];
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R adjugate_t(const R J[3][3], R adj[3][3]) {
+  adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+}
+
+template <typename R>
+__device__ __forceinline__ void wht8_t(R x[8]) {
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; i += 2 * h)
+#pragma unroll
+      for (int j = i; j < i + h; ++j) {
+        const R a = x[j], b = x[j + h];
+        x[j] = a + b;
+        x[j + h] = a - b;
+      }
+}
+
 // in-place 8-point Walsh-Hadamard transform y[n] = sum_S (-1)^popcount(n & S) x[S]
 __device__ __forceinline__ void wht8(double x[8]) {
 #pragma unroll
@@ -151,93 +279,97 @@ __device__ __forceinline__ void wht8(double x[8]) {
       }
 }
 
+template <typename R>
 __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny, int nz,
                                                           const double* __restrict__ X,
                                                           const double* __restrict__ Y,
                                                           const double* __restrict__ Z,
+                                                          const float2* __restrict__ xyz2,
                                                           double d0, double d1, double d2,
                                                           double* __restrict__ C, int* flag,
                                                           int cls) {
   int i, j, k;
   if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
-  Geo G;
-  load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
-  // C_g = adj D adj^T / det at the 8 Gauss points (6 symmetric components)
-  double Ch[8][6];
+  R Ch[8][6];
   bool bad = false;
+  {
+    GeoT<R> G;
+    load_geo_t<R>(X, Y, Z, xyz2, (int64_t)(nx + 1) * (ny + 1) * (nz + 1), nx + 1, ny + 1, i, j, k, G);
+    R Jc[3][4][3];
+    jac_columns<R>(G, Jc);
+    const R D[3] = {Num<R>::from(d0), Num<R>::from(d1), Num<R>::from(d2)};
+    // C_g = adj D adj^T / det at the 8 Gauss points (6 symmetric components)
 #pragma unroll
-  for (int gp = 0; gp < 8; ++gp) {
-    double xi[3], J[3][3], adj[3][3];
-    gauss_xi(gp, xi);
-    jacobian_at(G, xi, J);
-    const double det = adjugate(J, adj);
-    bad |= !(det > 0.0);
-    const double inv = 1.0 / det;
-    double aD[3][3];
+    for (int gp = 0; gp < 8; ++gp) {
+      R J[3][3], adj[3][3];
+      jac_at_gauss<R>(Jc, gp, J);
+      const R det = adjugate_t<R>(J, adj);
+      bad |= !Num<R>::pos(det);
+      const R inv = Num<R>::rcp(det);
+      R aD[3][3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      aD[r][0] = adj[r][0] * d0;
-      aD[r][1] = adj[r][1] * d1;
-      aD[r][2] = adj[r][2] * d2;
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) aD[r][t] = adj[r][t] * D[t];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int t = r; t < 3; ++t)
+          Ch[gp][sym6(r, t)] = (aD[r][0] * adj[t][0] + aD[r][1] * adj[t][1] + aD[r][2] * adj[t][2]) * inv;
     }
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int t = r; t < 3; ++t)
-        Ch[gp][sym6(r, t)] =
-            (aD[r][0] * adj[t][0] + aD[r][1] * adj[t][1] + aD[r][2] * adj[t][2]) * inv;
-  }
-  // sign sums over the Gauss points: sum_g sigma_q(g) C_g = (-1)^|q| (W C)[q]
-  // (the sign is applied where the sums are used)
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    double v[8];
-#pragma unroll
-    for (int gp = 0; gp < 8; ++gp) v[gp] = Ch[gp][c];
-    wht8(v);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) Ch[q][c] = v[q];
   }
   if (bad) atomicOr(flag, 1);
-  // K~ = D K^ D / 64 (D[S] = (-1)^|S|); row and column 0 vanish
-  double Kt[8][8];
+  // sign sums over the Gauss points: sum_g sigma_q(g) C_g = (-1)^|q| (W C)[q]
 #pragma unroll
-  for (int S = 0; S < 8; ++S)
+  for (int c = 0; c < 6; ++c) {
+    R v[8];
 #pragma unroll
-    for (int T = 0; T < 8; ++T) {
-      if (S == 0 || T == 0 || T < S) continue;
-      double v = 0.0;
+    for (int gp = 0; gp < 8; ++gp) v[gp] = Ch[gp][c];
+    wht8_t<R>(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Ch[q][c] = (popc3(q) & 1) ? -v[q] : v[q];
+  }
+  // K~ = D K^ D / 64 (D[S] = (-1)^|S|), upper triangle; row and column 0 vanish
+  R Kt[8][8];
+#pragma unroll
+  for (int S = 1; S < 8; ++S)
+#pragma unroll
+    for (int T = S; T < 8; ++T) {
+      R v = Num<R>::from(0.0);
+      bool first = true;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (!((S >> a) & 1)) continue;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
           if (!((T >> b) & 1)) continue;
-          const int q = (S & ~(1 << a)) ^ (T & ~(1 << b));
-          v += (popc3(q) & 1) ? -Ch[q][sym6(a, b)] : Ch[q][sym6(a, b)];
+          const R t = Ch[(S & ~(1 << a)) ^ (T & ~(1 << b))][sym6(a, b)];
+          v = first ? t : v + t;
+          first = false;
         }
       }
       const int e = popc3(S) + popc3(T);
-      Kt[S][T] = v * (spow(e - 2) * ((e & 1) ? -1.0 : 1.0) / 64.0);
+      Kt[S][T] = v * Num<R>::from(spow(e - 2) * ((e & 1) ? -1.0 : 1.0) / 64.0);
     }
+  // K_e = W K~ W: transform the rows, then the columns (only m <= n is kept)
 #pragma unroll
   for (int S = 0; S < 8; ++S)
 #pragma unroll
     for (int T = 0; T < 8; ++T) {
-      if (S == 0 || T == 0) Kt[S][T] = 0.0;
+      if (S == 0 || T == 0) Kt[S][T] = Num<R>::from(0.0);
       else if (T < S) Kt[S][T] = Kt[T][S];
     }
-  // K_e = W K~ W: transform the rows, then the columns
 #pragma unroll
-  for (int S = 1; S < 8; ++S) wht8(Kt[S]);
+  for (int S = 1; S < 8; ++S) wht8_t<R>(Kt[S]);
+  double Ke[8][8];
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
-    double col[8];
+    R col[8];
 #pragma unroll
     for (int S = 0; S < 8; ++S) col[S] = Kt[S][n];
-    wht8(col);
+    wht8_t<R>(col);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) Kt[m][n] = col[m];
+    for (int m = 0; m <= n; ++m) Ke[m][n] = Num<R>::to(col[m]);
   }
   // scatter: row of local node m gets Ke[m][n] at offset (n - m)
 #pragma unroll
@@ -251,95 +383,70 @@ __global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny
       if (!is_free(g, in, jn, kn)) continue;
       int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
               9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-      C[(int64_t)s * g.total + row] += (n >= m) ? Kt[m][n] : Kt[n][m];
+      C[(int64_t)s * g.total + row] += (n >= m) ? Ke[m][n] : Ke[n][m];
     }
   }
 }
 
-// out[m] = sum_g dN_m(g) . (adj(J_g) v_g) for the 8 local nodes (v_g supplied by
-// Vsrc): with w^_q = sum_g sigma_q(g) w_g the modal load is
+// out[m] = sum_g dN_m(g) . (adj(J_g) v_g) for the 8 local nodes, v_g given at
+// the Gauss points: with w^_q = sum_g sigma_q(g) w_g the modal load is
 // f^[S] = s^(|S|-1) sum_{a in S} w^_{S\a}[a] and out = 1/8 H f^.
-// quad 1 is the one-point rule at the center (weight 8): out[m] = eps_m . (adj(J_0) v_0).
-template <typename Vsrc>
-__device__ __forceinline__ void weak_div_elem(const Geo& G, int quad, const Vsrc& vsrc,
-                                              double out[8]) {
-  if (quad != 0) {
-    double xi[3] = {0.0, 0.0, 0.0}, J[3][3], adj[3][3], v[3], w[3];
-    jacobian_at(G, xi, J);
-    adjugate(J, adj);
-    vsrc(0, xi, v);
-#pragma unroll
-    for (int r = 0; r < 3; ++r) w[r] = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
-#pragma unroll
-    for (int m = 0; m < 8; ++m)
-      out[m] = ((m & 1) ? w[0] : -w[0]) + ((m & 2) ? w[1] : -w[1]) + ((m & 4) ? w[2] : -w[2]);
-    return;
-  }
-  double wh[8][3];
+template <typename R>
+__device__ __forceinline__ void weak_div_modal(const GeoT<R>& G, const R vg[8][3], double out[8]) {
+  R Jc[3][4][3];
+  jac_columns<R>(G, Jc);
+  R wh[8][3];
 #pragma unroll
   for (int gp = 0; gp < 8; ++gp) {
-    double xi[3], J[3][3], adj[3][3], v[3];
-    gauss_xi(gp, xi);
-    jacobian_at(G, xi, J);
-    adjugate(J, adj);
-    vsrc(gp, xi, v);
+    R J[3][3], adj[3][3];
+    jac_at_gauss<R>(Jc, gp, J);
+    adjugate_t<R>(J, adj);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) wh[gp][r] = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
+    for (int r = 0; r < 3; ++r)
+      wh[gp][r] = adj[r][0] * vg[gp][0] + adj[r][1] * vg[gp][1] + adj[r][2] * vg[gp][2];
   }
-  // sign sums over the Gauss points, (-1)^|q| (W w)[q] (sign applied below)
+  // sign sums over the Gauss points, (-1)^|q| (W w)[q]
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    double t[8];
+    R t[8];
 #pragma unroll
     for (int gp = 0; gp < 8; ++gp) t[gp] = wh[gp][r];
-    wht8(t);
+    wht8_t<R>(t);
 #pragma unroll
     for (int q = 0; q < 8; ++q) wh[q][r] = (popc3(q) & 1) ? -t[q] : t[q];
   }
   // f~[S] = (-1)^|S| f^[S] / 8, then out = W f~
+  R fv[8];
+  fv[0] = Num<R>::from(0.0);
 #pragma unroll
-  for (int S = 0; S < 8; ++S) {
-    double v = 0.0;
+  for (int S = 1; S < 8; ++S) {
+    R v = Num<R>::from(0.0);
+    bool first = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if ((S >> a) & 1) v += wh[S & ~(1 << a)][a];
+      if ((S >> a) & 1) {
+        v = first ? wh[S & ~(1 << a)][a] : v + wh[S & ~(1 << a)][a];
+        first = false;
+      }
     const int e = popc3(S);
-    out[S] = S == 0 ? 0.0 : v * (spow(e - 1) * ((e & 1) ? -1.0 : 1.0) * 0.125);
+    fv[S] = v * Num<R>::from(spow(e - 1) * ((e & 1) ? -1.0 : 1.0) * 0.125);
   }
-  wht8(out);
+  wht8_t<R>(fv);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) out[m] = Num<R>::to(fv[m]);
 }
 
-struct CenterValue {
-  double v0[3];
-  __device__ void operator()(int, const double*, double v[3]) const {
-    v[0] = v0[0];
-    v[1] = v0[1];
-    v[2] = v0[2];
-  }
-};
-
-struct NodalInterp {
-  double ue[8][3];
-  __device__ void operator()(int, const double xi[3], double v[3]) const {
-    v[0] = v[1] = v[2] = 0.0;
+// one-point rule at the center (weight 8): out[m] = eps_m . (adj(J_0) v_0)
+__device__ __forceinline__ void weak_div_center(const Geo& G, const double v[3], double out[8]) {
+  double xi[3] = {0.0, 0.0, 0.0}, J[3][3], adj[3][3], w[3];
+  jacobian_at(G, xi, J);
+  adjugate(J, adj);
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      double N = shape(n, xi);
-      v[0] += N * ue[n][0];
-      v[1] += N * ue[n][1];
-      v[2] += N * ue[n][2];
-    }
-  }
-};
-
-struct GaussValues {
-  const double* ug;
-  int64_t e, NE;
-  __device__ void operator()(int gp, const double*, double v[3]) const {
+  for (int r = 0; r < 3; ++r) w[r] = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) v[d] = ug[((int64_t)d * 8 + gp) * NE + e];
-  }
-};
+  for (int m = 0; m < 8; ++m)
+    out[m] = ((m & 1) ? w[0] : -w[0]) + ((m & 2) ? w[1] : -w[1]) + ((m & 4) ? w[2] : -w[2]);
+}
 
 __device__ __forceinline__ void load_u(const double* u0, int64_t N, int nx1, int ny1, int i,
                                        int j, int k, double ue[8][3]) {
@@ -352,33 +459,100 @@ __device__ __forceinline__ void load_u(const double* u0, int64_t N, int nx1, int
   }
 }
 
+// nodal values -> values at the 8 Gauss points, u(g) = 1/8 W (s^|S| (W u)):
+// the trilinear interpolant's modal coefficients evaluated at xi = +-s.
+template <typename R>
+__device__ __forceinline__ void interp_gauss_modal(const R ue[8][3], R vg[8][3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R t[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) t[n] = ue[n][d];
+    wht8_t<R>(t);
+#pragma unroll
+    for (int S = 0; S < 8; ++S) t[S] = t[S] * Num<R>::from(spow(popc3(S)) * 0.125);
+    wht8_t<R>(t);
+#pragma unroll
+    for (int gp = 0; gp < 8; ++gp) vg[gp][d] = t[gp];
+  }
+}
+
+template <typename R>
 __global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, int nz,
                                                       const double* __restrict__ X,
                                                       const double* __restrict__ Y,
                                                       const double* __restrict__ Z,
-                                                      const double* __restrict__ u0, int quad,
+                                                      const float2* __restrict__ xyz2,
+                                                      const double* __restrict__ u0,
+                                                      const float2* __restrict__ u2, int quad,
                                                       double* __restrict__ f, int cls) {
   int i, j, k;
   if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
-  Geo G;
-  load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
   double fe[8];
-  if (quad & 2) {
-    // u0 given at the element centers: constant over the element
-    const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
-    CenterValue src{{u0[e], u0[NE + e], u0[2 * NE + e]}};
-    weak_div_elem(G, quad & 1, src, fe);
+  const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
+  const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  if (quad & 1) {
+    Geo G;
+    load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
+    double v[3];
+    if (quad & 2) {
+      v[0] = u0[e]; v[1] = u0[NE + e]; v[2] = u0[2 * NE + e];
+    } else {
+      double ue[8][3];
+      load_u(u0, N, nx + 1, ny + 1, i, j, k, ue);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double sum = 0.0;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) sum += ue[n][d];
+        v[d] = 0.125 * sum;
+      }
+    }
+    weak_div_center(G, v, fe);
   } else {
-    NodalInterp src;
-    int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-    load_u(u0, N, nx + 1, ny + 1, i, j, k, src.ue);
-    weak_div_elem(G, quad & 1, src, fe);
+    GeoT<R> G;
+    load_geo_t<R>(X, Y, Z, xyz2, N, nx + 1, ny + 1, i, j, k, G);
+    R vg[8][3];
+    if (quad & 2) {
+      // u0 given at the element centers: constant over the element
+      const R c0 = Num<R>::from(u0[e]), c1 = Num<R>::from(u0[NE + e]), c2 = Num<R>::from(u0[2 * NE + e]);
+#pragma unroll
+      for (int gp = 0; gp < 8; ++gp) { vg[gp][0] = c0; vg[gp][1] = c1; vg[gp][2] = c2; }
+    } else {
+      R ue[8][3];
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const int64_t id = sidx(nx + 1, ny + 1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if constexpr (__is_same(R, dflt)) {
+            const float2 v = u2[d * N + id];
+            ue[n][d] = R{v.x, v.y};
+          } else {
+            ue[n][d] = u0[d * N + id];
+          }
+        }
+      }
+      interp_gauss_modal<R>(ue, vg);
+    }
+    weak_div_modal<R>(G, vg, fe);
   }
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
     if (!is_free(g, im, jm, km)) continue;
     f[gidx(g, im, jm, km)] -= fe[m];
+  }
+}
+
+// float64 -> (hi, lo) float pairs, n values
+__global__ void k_split_pairs(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; t < n; t += st) {
+    const double v = a[t];
+    const float h = (float)v;
+    b[t] = make_float2(h, (float)(v - (double)h));
   }
 }
 
@@ -392,9 +566,14 @@ __global__ void __launch_bounds__(128) k_weak_div(int nx, int ny, int nz,
   if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
   Geo G;
   load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
-  GaussValues src{ug, ((int64_t)k * ny + j) * nx + i, (int64_t)nx * ny * nz};
+  const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
+  double vg[8][3];
+#pragma unroll
+  for (int gp = 0; gp < 8; ++gp)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) vg[gp][d] = ug[((int64_t)d * 8 + gp) * NE + e];
   double be[8];
-  weak_div_elem(G, 0, src, be);
+  weak_div_modal<double>(G, vg, be);
 #pragma unroll
   for (int m = 0; m < 8; ++m)
     out[sidx(nx + 1, ny + 1, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] += be[m];
@@ -617,28 +796,44 @@ dim3 elem_grid(int nx, int ny, int nz, int cls, dim3 blk) {
 
 }  // namespace
 
+cudaError_t launch_split_pairs(const double* a, float2* b, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_split_pairs<<<blocks, 256, 0, st>>>(a, b, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble_stencil(const Grid& g, int nx, int ny, int nz, const double* X,
-                                    const double* Y, const double* Z, const double* a,
-                                    double* C, int* flag, cudaStream_t st) {
+                                    const double* Y, const double* Z, const float2* xyz2,
+                                    const double* a, double* C, int* flag, int dfloat,
+                                    cudaStream_t st) {
   dim3 blk(32, 4, 1);
   for (int cls = 0; cls < 8; ++cls) {
     dim3 grd = elem_grid(nx, ny, nz, cls, blk);
     if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
-    k_assemble_stencil<<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, 1.0 / (a[0] * a[0]),
-                                            1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), C, flag,
-                                            cls); count_launches(1);
+    const double d0 = 1.0 / (a[0] * a[0]), d1 = 1.0 / (a[1] * a[1]), d2 = 1.0 / (a[2] * a[2]);
+    if (dfloat)
+      k_assemble_stencil<dflt><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, d0, d1, d2, C, flag, cls);
+    else
+      k_assemble_stencil<double><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, d0, d1, d2, C, flag, cls);
+    count_launches(1);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_rhs(const Grid& g, int nx, int ny, int nz, const double* X,
-                                const double* Y, const double* Z, const double* u0, int quad,
-                                double* f, cudaStream_t st) {
+                                const double* Y, const double* Z, const float2* xyz2,
+                                const double* u0, const float2* u2, int quad, double* f,
+                                int dfloat, cudaStream_t st) {
   dim3 blk(32, 4, 1);
   for (int cls = 0; cls < 8; ++cls) {
     dim3 grd = elem_grid(nx, ny, nz, cls, blk);
     if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
-    k_assemble_rhs<<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, u0, quad, f, cls); count_launches(1);
+    if (dfloat)
+      k_assemble_rhs<dflt><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, u0, u2, quad, f, cls);
+    else
+      k_assemble_rhs<double><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, u0, u2, quad, f, cls);
+    count_launches(1);
   }
   return cudaGetLastError();
 }

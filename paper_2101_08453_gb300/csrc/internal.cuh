@@ -137,6 +137,7 @@ struct mcwind_plan_s {
   size_t off_scalars = 0;                   // device scalars / flags
   size_t off_cfree = 0;                     // coarsest free-node grid indices
   size_t off_cg = 0;                        // 6 finest-level float64 vectors of CG
+  size_t off_xyz2 = 0, off_u2 = 0;          // X, Y, Z and u0 as float pairs [3][nodes]
   size_t off_adj = 0;                       // adjoint reduction partials (6 per block) + sums
   int n_adj = 0;
   int n_coarse = 0;

@@ -7,15 +7,22 @@ namespace mcw {
 // ---- element.cu: isoparametric trilinear hexahedra (Sec. 2) ----
 // Stiffness (Eq. 5 left side, 2x2x2 Gauss) scattered into the 28-plane
 // stencil of level 0 (planes must be zero on entry); flag |= 1 on detJ <= 0.
+// dfloat: element arithmetic in float pairs (FP32 pipe) instead of double.
+// xyz2: X, Y, Z split into (hi, lo) float pairs, [3][nodes] (read when dfloat)
 cudaError_t launch_assemble_stencil(const Grid& g, int nx, int ny, int nz, const double* X,
-                                    const double* Y, const double* Z, const double* a,
-                                    double* C, int* flag, cudaStream_t st);
+                                    const double* Y, const double* Z, const float2* xyz2,
+                                    const double* a, double* C, int* flag, int dfloat,
+                                    cudaStream_t st);
+// float64 -> (hi, lo) float pairs
+cudaError_t launch_split_pairs(const double* a, float2* b, int64_t n, cudaStream_t st);
 // Load vector (Eq. 5 right side) into f (split layout, zero on entry).
 // quad bit 0: one-point center rule; bit 1: u0 given at the element centers
 // ([3][nz][ny][nx]) instead of at the nodes.
+// u2: nodal u0 split into float pairs (read when dfloat with nodal u0)
 cudaError_t launch_assemble_rhs(const Grid& g, int nx, int ny, int nz, const double* X,
-                                const double* Y, const double* Z, const double* u0, int quad,
-                                double* f, cudaStream_t st);
+                                const double* Y, const double* Z, const float2* xyz2,
+                                const double* u0, const float2* u2, int quad, double* f,
+                                int dfloat, cudaStream_t st);
 // u = u0 + A^{-1} grad lambda (Eq. 3); lambda in split layout.
 cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* X,
                            const double* Y, const double* Z, const double* u0,

@@ -107,6 +107,7 @@ extern "C" void mcwind_default_options(mcwind_options* o) {
   o->accel = MCWIND_ACCEL_NONE;
   o->use_graphs = 1;
   o->u0_at = MCWIND_U0_NODES;
+  o->element_arith = MCWIND_ARITH_DFLOAT;
 }
 
 extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], double h1,
@@ -138,6 +139,7 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   if (o.accel == MCWIND_ACCEL_CG && o.post_reverse != 1) return MCWIND_EINVAL;
   if (o.use_graphs != 0 && o.use_graphs != 1) return MCWIND_EINVAL;
   if (o.u0_at != MCWIND_U0_NODES && o.u0_at != MCWIND_U0_CENTERS) return MCWIND_EINVAL;
+  if (o.element_arith != MCWIND_ARITH_F64 && o.element_arith != MCWIND_ARITH_DFLOAT) return MCWIND_EINVAL;
 
   std::vector<PlanLevel> H = hierarchy(nx, ny, nz, a, h1, h3, o.coarsen_rule, o.coarsest_max);
   if (H.empty() || !H.back().kmap.empty()) return MCWIND_EINVAL;
@@ -196,6 +198,13 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
     const size_t t0 = (size_t)p->lv[0].g.total;
     p->off_cg = off;
     off = align256(off + 6 * align256(t0 * 8));
+  }
+  {
+    const size_t nodes = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+    p->off_xyz2 = off;
+    off = align256(off + 3 * nodes * sizeof(float2));
+    p->off_u2 = off;
+    off = align256(off + 3 * nodes * sizeof(float2));
   }
   p->n_adj = adjoint_partials(nx, ny, nz);
   p->off_adj = off;

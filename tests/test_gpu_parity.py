@@ -72,7 +72,7 @@ def test_stencil_all_levels(torch, name):
 
 
 def test_stencil_f64_ulp_level_on_fine_grid(torch):
-    c, plan, _, H = setup(torch, "hill64")
+    c, plan, _, H = setup(torch, "hill64", element_arith=m.ARITH_F64)
     dims = level_dims(plan, 0)
     ref = stencil_planes(H.K[0], dims)
     out = torch.empty((27, ref.shape[1]), dtype=torch.float64, device="cuda")
@@ -371,3 +371,23 @@ def test_wind_at_centers(torch, quad):
     assert rel(lam.cpu().numpy().ravel(), lam_ref) <= 1e-10
     u = plan.recover(ucd, lam).cpu().numpy()
     assert rel(u, oracle.recover_centers(c, lam_ref, uc)) <= 1e-10
+
+
+@pytest.mark.parametrize("arith,tol", [(m.ARITH_F64, 1e-13), (m.ARITH_DFLOAT, 1e-12)])
+@pytest.mark.parametrize("name", ["ragged", "jitter", "aniso"])
+def test_element_arithmetic(torch, arith, tol, name):
+    """Stiffness and load vector in float64 and in float pairs against the
+    oracle; both give the oracle's solution to 1e-10."""
+    c, plan, (X, Y, Z, u0), H = setup(torch, name, coarsest_max=1024, element_arith=arith)
+    dims = level_dims(plan, 0)
+    ref = stencil_planes(H.K[0], dims)
+    out = torch.empty((27, ref.shape[1]), dtype=torch.float64, device="cuda")
+    m.mcwind_level_stencil(plan.handle, 0, m.PREC_F64, out)
+    assert np.abs(out.cpu().numpy() - ref).max() <= tol * np.abs(ref[13]).max()
+    f_ref = np.where(oracle.case_free_mask(c), oracle.assemble_f(c), 0.0)
+    f = plan.rhs(u0).cpu().numpy().ravel()
+    assert np.abs(f - f_ref).max() <= tol * np.abs(f_ref).max()
+    lam, st = plan.solve(u0, rtol=1e-12, max_cycles=120)
+    if name not in _lam_ref:
+        _lam_ref[name] = oracle.solve(c)
+    assert rel(lam.cpu().numpy().ravel(), _lam_ref[name]) <= 1e-10
