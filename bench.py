@@ -37,10 +37,13 @@ CELLS = (3000, 3000, 15)
 RTOL = 1e-8
 SAMPLE_W = 160       # CPU baseline / reference window (cells per side)
 SAMPLE_I0, SAMPLE_J0 = 1420, 1420
-# FP64-pipe thread instructions per element of the element kernels (modal form), as
-# counted by ncu (smsp__sass_thread_inst_executed_op_fp64 / elements) on a small case
-FP64_OPS_STIFFNESS = 1213.0
-FP64_OPS_LOAD = 665.0
+# FP32-pipe thread instructions per element of the element kernels in float-pair
+# arithmetic (the default), counted by ncu (sm__inst_executed_pipe_fma x 32 / elements)
+# on one element-parity launch of the 600x600x15 case (720000 elements)
+FP32_OPS_STIFFNESS = 14198.0
+FP32_OPS_LOAD = 8308.0
+# FP32 pipe: 128 lanes per SM x 152 SMs x 2.07 GHz maximum SM clock
+FP32_PIPE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per unit of a launch, from one ncu capture of the
 # 600x600x15 case (profiles/k_gs_float_600x600x15.md), scaled by the units of
 # the full launch: FP32 smoother, bytes per node of the column group.
@@ -62,6 +65,9 @@ def parse():
     ap.add_argument("--workload", default="domain", choices=["domain", "batched", "rates"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--launch-summary", default=None, metavar="CSV",
+                    help="print per-kernel launches, time and share from an ncu "
+                         "--metrics gpu__time_duration.sum --csv log, then exit")
     return ap.parse_args()
 
 
@@ -329,8 +335,38 @@ def bench_rates(args):
     return 0
 
 
+def launch_summary(path):
+    """Per-kernel launches, total device time and share of an ncu launch list."""
+    import collections
+    import csv
+    rows = list(csv.reader(open(path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Value" in r)
+    h = rows[hi]
+    ki, mi, vi, ui = (h.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
+    scale = {"nsecond": 1e-6, "ns": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0,
+             "ms": 1.0, "second": 1e3}
+    tot, cnt = collections.defaultdict(float), collections.Counter()
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
+            continue
+        name = r[ki]
+        for pre in ("void ", "mcw::", "<unnamed>::", "unnamed>::", "(anonymous namespace)::"):
+            name = name.replace(pre, "")
+        name = name.split("(")[0]
+        tot[name] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1e-6)
+        cnt[name] += 1
+    total = sum(tot.values())
+    print(f"| kernel | launches | total ms | share |\n|---|---:|---:|---:|")
+    for k, v in sorted(tot.items(), key=lambda kv: -kv[1]):
+        print(f"| `{k}` | {cnt[k]} | {v:.2f} | {100 * v / total:.1f}% |")
+    print(f"| total | {sum(cnt.values())} | {total:.2f} | 100% |")
+    return 0
+
+
 def main():
     args = parse()
+    if args.launch_summary:
+        return launch_summary(args.launch_summary)
     if args.workload == "batched" and args.impl != "reference":
         return bench_batched(args)
     if args.workload == "rates" and args.impl != "reference":
@@ -412,12 +448,14 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     w0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed_steps")   # lets ncu --nvtx-include select the timed steps
     e0.record()
     cycles = []
     for s in range(args.steps):
         s1, s2 = step(ev=phase_ev[s])
         cycles.append((s1.cycles, s2.cycles, s1.rel_res, s2.rel_res, s1.rate, s2.rate))
     e1.record()
+    torch.cuda.nvtx.range_pop()
     barrier()
     wall = time.perf_counter() - w0
     launches = m.lib().mcwind_launch_count() - l0
@@ -530,43 +568,43 @@ def main():
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # FP64 pipe: 2 FP64 FMA per clock per SM, measured 5.81e11 FP64 FMA/s on this GB300
-    fp64_peak = 0.581   # T FP64 operations/s (one add, mul or FMA per pipe slot)
     plan_dims = (nx + 1, ny + 1, nz + 1)
     n_nodes = plan_dims[0] * plan_dims[1] * plan_dims[2]
     n_elem = nx * ny * nz
 
     def algo_units(cs, mixed):
-        """Algorithmic units of one launch of each class (derivations in the design doc)."""
+        """Algorithmic units of one launch (HBM classes) or one call (element classes:
+        3 + 8 or 1 + 8 launches, the input splits into float pairs and the 8
+        element-parity launches) of each class (derivations in the design doc)."""
         return {
             # bytes: 26 off-diagonal coefficients + 1/diagonal + f + x read + x write per
             # free node of one column group
-            "smooth_fine": ("hbm", (27 * cs + 3 * cs) * n_free / 4.0),
-            "residual_fine": ("hbm", (27 * cs + 3 * cs) * n_free),
+            "smooth_fine": ("hbm", (27 * cs + 3 * cs) * n_free / 4.0, 1),
+            "residual_fine": ("hbm", (27 * cs + 3 * cs) * n_free, 1),
             # float64 residual: 27 coefficients + f + x + r out (+ float32 r and e out when mixed)
-            "outer_residual": ("hbm", (27 * 8 + 3 * 8 + (8 if mixed else 0)) * n_free),
-            # FP64 operations of one element-parity launch (modal form, counted by ncu as
-            # FP64-pipe thread instructions per element): stiffness and load vector
-            "assemble": ("alu", FP64_OPS_STIFFNESS * n_elem / 8.0),
-            "rhs": ("alu", FP64_OPS_LOAD * n_elem / 8.0),
+            "outer_residual": ("hbm", (27 * 8 + 3 * 8 + (8 if mixed else 0)) * n_free, 1),
+            # FP32-pipe operations of all elements (float pairs, modal form, counted by
+            # ncu per element): stiffness and load vector
+            "assemble": ("alu", FP32_OPS_STIFFNESS * n_elem, 11),
+            "rhs": ("alu", FP32_OPS_LOAD * n_elem, 9),
         }
 
     def roofs(profile, cs, mixed):
         out = {}
-        for k, (bound, units) in algo_units(cs, mixed).items():
+        for k, (bound, units, per_call) in algo_units(cs, mixed).items():
             ms, n = profile[k]
-            if n == 0:
+            if n == 0 or n % per_call:
                 continue
-            per = ms / n / 1e3
+            per = ms / (n // per_call) / 1e3
             if bound == "hbm":
                 ach = units / per / 1e9
                 out[k] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                           "frac": ach / hbm_peak, "ms_per_launch": per * 1e3, "launches": n}
             else:
                 ach = units / per / 1e12
-                out[k] = {"bound": "alu", "achieved": ach, "peak": fp64_peak,
-                          "unit": "T FP64 op/s", "frac": ach / fp64_peak,
-                          "ms_per_launch": per * 1e3, "launches": n}
+                out[k] = {"bound": "alu", "achieved": ach, "peak": FP32_PIPE_PEAK_T,
+                          "unit": "T FP32-pipe op/s", "frac": ach / FP32_PIPE_PEAK_T,
+                          "ms_per_call": per * 1e3, "launches": n}
         return out
 
     mixed = prec == m.PREC_MIXED
@@ -582,7 +620,7 @@ def main():
         dom_roof["traffic_source"] = how
     dom_roof["peak_source"] = ("measured: MEASURED_PEAKS.json hbm_gbs (burst copy)"
                                if dom_roof.get("bound") == "hbm"
-                               else "measured: FP64 FMA issue rate of this GB300, 5.81e11/s")
+                               else "FP32 pipe: 128 lanes x 152 SMs x 2.07 GHz")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -616,6 +654,8 @@ def main():
         "roofline_kernels": roof_kernels,
         "roofline_kernels_f64_solve": roof_f64,
         "profile_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof_main.items() if v[1]},
+        "profile_ms_f64_solve": ({k: {"ms": v[0], "launches": v[1]} for k, v in prof_f64.items()
+                                  if v[1]} if prof_f64 else None),
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,

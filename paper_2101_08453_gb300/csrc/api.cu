@@ -142,21 +142,31 @@ double* dense_inv(mcwind_plan p) {
   return (p->n_coarse % 2 == 0) ? A : A + (size_t)p->n_coarse * p->n_coarse;
 }
 
+// sweeps of the column Gauss-Seidel smoother on level l; zero_start: x is 0
+// on entry (or, for a forward sweep, need not be zeroed: the first group
+// writes all of x)
 template <typename T>
-int smooth(mcwind_plan p, int l, int sweeps, int direction, cudaStream_t st) {
+int smooth(mcwind_plan p, int l, int sweeps, int direction, cudaStream_t st,
+           bool zero_start = false) {
   auto P = Sel<T>::get(p, l);
   const Grid& g = p->lv[l].g;
   PROF(l == 0 ? MCWIND_K_SMOOTH_FINE : MCWIND_K_SMOOTH_COARSE);
   for (int s = 0; s < sweeps; ++s)
     for (int q = 0; q < 4; ++q) {
       const int grp = direction == MCWIND_FORWARD ? q : 3 - q;
-      CK(launch_gs_group<T>(g, P.C, P.f, P.x, grp, direction == MCWIND_FORWARD ? 1 : 0, p->gs_rows, st));
+      if (s == 0 && q == 0 && zero_start && direction == MCWIND_FORWARD)
+        CK(launch_gs_zero_start<T>(g, P.C, P.f, P.x, grp, st));
+      else
+        CK(launch_gs_group<T>(g, P.C, P.f, P.x, grp, direction == MCWIND_FORWARD ? 1 : 0,
+                              p->gs_rows, st));
     }
   return MCWIND_OK;
 }
 
+// one V-cycle from level l down; x_zero: the level-0 x is 0 on entry (the
+// coarser levels always start from 0)
 template <typename T>
-int vcycle(mcwind_plan p, int l, cudaStream_t st) {
+int vcycle(mcwind_plan p, int l, cudaStream_t st, bool x_zero = false) {
   const int last = (int)p->lv.size() - 1;
   auto P = Sel<T>::get(p, l);
   Level& L = p->lv[l];
@@ -165,8 +175,9 @@ int vcycle(mcwind_plan p, int l, cudaStream_t st) {
     CK(launch_dense_solve<T>(dense_inv(p), p->n_coarse, cfree(p), P.f, P.x, st));
     return MCWIND_OK;
   }
-  if (l > 0) CK(cudaMemsetAsync(P.x, 0, sizeof(T) * (size_t)L.g.total, st));
-  CKR(smooth<T>(p, l, p->opt.nu_pre, MCWIND_FORWARD, st));
+  const bool zs = (l > 0 || x_zero) && p->opt.nu_pre >= 1;
+  if (l > 0 && !zs) CK(cudaMemsetAsync(P.x, 0, sizeof(T) * (size_t)L.g.total, st));
+  CKR(smooth<T>(p, l, p->opt.nu_pre, MCWIND_FORWARD, st, zs));
   {
     PROF(l == 0 ? MCWIND_K_RESIDUAL_FINE : MCWIND_K_RESIDUAL_COARSE);
     CK(launch_residual<T>(L.g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
@@ -176,7 +187,7 @@ int vcycle(mcwind_plan p, int l, cudaStream_t st) {
     PROF(MCWIND_K_RESTRICT);
     CK(launch_restrict<T>(L.g, p->lv[l + 1].g, L.tr, P.r, Q.f, st));
   }
-  CKR(vcycle<T>(p, l + 1, st));
+  CKR(vcycle<T>(p, l + 1, st, true));
   {
     PROF(MCWIND_K_PROLONG);
     CK(launch_prolong_add<T>(L.g, p->lv[l + 1].g, L.tr, Q.x, P.x, st));
@@ -227,7 +238,7 @@ int one_cycle(mcwind_plan p, cudaStream_t st) {
   if (p->opt.precision == MCWIND_PREC_F64) {
     CKR(vcycle<double>(p, 0, st));
   } else {
-    CKR(vcycle<float>(p, 0, st));
+    CKR(vcycle<float>(p, 0, st, true));  // the outer residual zeroed the correction
     PROF(MCWIND_K_UPDATE);
     CK(launch_update_mixed(p->lv[0].g, lv64(p, 0).x, lv32(p, 0).x, st));
   }
@@ -432,7 +443,7 @@ int cg_true_residual(mcwind_plan p, const CgVec& v, cudaStream_t st) {
 // one preconditioned CG iteration; ||r||^2 (recursive) into scal[1]
 template <typename T>
 int cg_iteration(mcwind_plan p, const CgVec& v, cudaStream_t st) {
-  CKR(vcycle<T>(p, 0, st));
+  CKR(vcycle<T>(p, 0, st, true));  // the preconditioner input starts at 0
   const Grid& g = p->lv[0].g;
   auto P = Sel<T>::get(p, 0);
   double* s = scal(p) + 4;
@@ -654,6 +665,21 @@ extern "C" int mcwind_recover(mcwind_plan p, const double* u0, const double* lam
   if (!p->assembled) return MCWIND_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   Level& L0 = p->lv[0];
+  if (where == MCWIND_AT_CENTERS && dfloat_elements(p)) {
+    // float pairs: lambda and a nodal u0 split in the [k][j][i] layout
+    float2* lam2 = (float2*)lv64(p, 0).r;  // scratch, >= nodes float pairs
+    float2* u2 = (float2*)(p->ws + p->off_u2);
+    const int64_t nn = (int64_t)std_nodes(p);
+    {
+      PROF(MCWIND_K_OTHER);
+      CK(launch_split_pairs(lambda, lam2, nn, st));
+      if (p->opt.u0_at == MCWIND_U0_NODES) CK(launch_split_pairs(u0, u2, 3 * nn, st));
+    }
+    PROF(MCWIND_K_RECOVER);
+    CK(launch_recover_center_df(p->nx, p->ny, p->nz, (const float2*)(p->ws + p->off_xyz2), u2,
+                                p->opt.u0_at == MCWIND_U0_NODES ? nullptr : u0, lam2, p->a, u, st));
+    return MCWIND_OK;
+  }
   double* lam = lv64(p, 0).r;  // scratch: lambda in the split layout
   {
     PROF(MCWIND_K_OTHER);

@@ -280,7 +280,7 @@ __device__ __forceinline__ void wht8(double x[8]) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_assemble_stencil(Grid g, int nx, int ny, int nz,
+__global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int ny, int nz,
                                                           const double* __restrict__ X,
                                                           const double* __restrict__ Y,
                                                           const double* __restrict__ Z,
@@ -545,15 +545,19 @@ __global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, in
   }
 }
 
-// float64 -> (hi, lo) float pairs, n values
+// float64 -> (hi, lo) float pairs, n values, split in integer arithmetic
+// (the double pipe would bound this copy), 4 values per thread and turn
 __global__ void k_split_pairs(const double* __restrict__ a, float2* __restrict__ b, int64_t n) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
-  for (; t < n; t += st) {
-    const double v = a[t];
-    const float h = (float)v;
-    b[t] = make_float2(h, (float)(v - (double)h));
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; t + 3 * st < n; t += 4 * st) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = a[t + q * st];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[t + q * st] = split_bits(v[q]);
   }
+  for (; t < n; t += st) b[t] = split_bits(a[t]);
 }
 
 __global__ void __launch_bounds__(128) k_weak_div(int nx, int ny, int nz,
@@ -634,6 +638,73 @@ __global__ void __launch_bounds__(128) k_recover(Grid g, int nx, int ny, int nz,
       double gd = (adj[0][d] * gr[0] + adj[1][d] * gr[1] + adj[2][d] * gr[2]) * inv;
       u[((int64_t)d * ng + gp) * NE + e] = up[d] + gd * dd[d];
     }
+  }
+}
+
+// Recovery at the element centers in float pairs: coordinates, lambda and a
+// nodal u0 pre-split into (hi, lo) pairs in the [k][j][i] layout.  At the
+// center the Jacobian columns are the edge means, dN_n/dxi_r = eps_{n,r}/8 and
+// N_n = 1/8.
+__global__ void __launch_bounds__(128) k_recover_center_df(int nx, int ny, int nz,
+                                                           const float2* __restrict__ xyz2,
+                                                           const float2* __restrict__ u2,
+                                                           const double* __restrict__ u0c,
+                                                           const float2* __restrict__ lam2,
+                                                           double d0, double d1, double d2,
+                                                           double* __restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= nx || j >= ny || k >= nz) return;
+  const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  GeoT<dflt> G;
+  load_geo_t<dflt>(nullptr, nullptr, nullptr, xyz2, N, nx + 1, ny + 1, i, j, k, G);
+  dflt J[3][3], adj[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      J[d][r] = ((G.e[r][0][d] + G.e[r][1][d]) + (G.e[r][2][d] + G.e[r][3][d])) * 0.125f;
+  const dflt inv = reciprocal(adjugate_t<dflt>(J, adj));
+  dflt le[8];
+  int64_t id[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    id[n] = sidx(nx + 1, ny + 1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
+    const float2 v = lam2[id[n]];
+    le[n] = dflt{v.x, v.y};
+  }
+  // reference gradient at the center: 1/8 sum_n eps_{n,r} lambda_n, i.e. 1/8 the
+  // sum of the 4 differences along the edges parallel to axis r
+  dflt gr[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int b = 1 << r;
+    dflt acc = le[b] - le[0];
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+      if (((n >> r) & 1) && n != b) acc = acc + (le[n] - le[n ^ b]);
+    gr[r] = acc * 0.125f;
+  }
+  const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
+  const double dd[3] = {d0, d1, d2};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dflt uc;
+    if (u0c) {
+      uc = df_of(u0c[d * NE + e]);
+    } else {
+      float2 v = u2[d * N + id[0]];
+      uc = dflt{v.x, v.y};
+#pragma unroll
+      for (int n = 1; n < 8; ++n) {
+        v = u2[d * N + id[n]];
+        uc = uc + dflt{v.x, v.y};
+      }
+      uc = uc * 0.125f;
+    }
+    const dflt gd = (adj[0][d] * gr[0] + adj[1][d] * gr[1] + adj[2][d] * gr[2]) * inv;
+    u[(int64_t)d * NE + e] = to_double(uc + gd * df_of(dd[d]));
   }
 }
 
@@ -891,6 +962,17 @@ cudaError_t launch_adjoint_finish(int nx, int ny, int nz, const double* X, const
     off += nb;
   }
   k_sum6<<<1, 32, 0, st>>>(partials, off, sums6);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover_center_df(int nx, int ny, int nz, const float2* xyz2, const float2* u2,
+                                     const double* u0c, const float2* lam2, const double* a,
+                                     double* u, cudaStream_t st) {
+  dim3 blk(32, 4, 1);
+  dim3 grd((nx + 31) / 32, (ny + 3) / 4, nz);
+  k_recover_center_df<<<grd, blk, 0, st>>>(nx, ny, nz, xyz2, u2, u0c, lam2, 1.0 / (a[0] * a[0]),
+                                           1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -28,6 +28,11 @@ cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* 
                            const double* Y, const double* Z, const double* u0,
                            const double* lam, const double* a, int where, int u0_centers,
                            double* u, cudaStream_t st);
+// recovery at the element centers in float pairs (xyz2, u2, lam2 pre-split in
+// the [k][j][i] layout; u0c != nullptr: u0 given at the centers instead of u2)
+cudaError_t launch_recover_center_df(int nx, int ny, int nz, const float2* xyz2, const float2* u2,
+                                     const double* u0c, const float2* lam2, const double* a,
+                                     double* u, cudaStream_t st);
 // adjoint of the recovery at element centers: h += G^T A^{-1} gu, du0 += C^T gu
 // (standard layouts, zero on entry)
 cudaError_t launch_recover_adjoint(int nx, int ny, int nz, const double* X, const double* Y,
@@ -66,6 +71,10 @@ cudaError_t launch_norm2_partials(const Grid& g, const double* v, double* partia
 
 // ---- smooth.cu: vertical Gauss-Seidel, one column group (Sec. 3) ----
 // rows: column rows per thread block (blockDim = 32 x rows, rows in 1..8)
+// first group of a forward sweep on x = 0: writes every entry of x
+template <typename T>
+cudaError_t launch_gs_zero_start(const Grid& g, const T* C, const T* f, T* x, int group,
+                                 cudaStream_t st);
 template <typename T>
 cudaError_t launch_gs_group(const Grid& g, const T* C, const T* f, T* x, int group, int up,
                             int rows, cudaStream_t st);

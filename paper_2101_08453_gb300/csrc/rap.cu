@@ -64,23 +64,62 @@ __global__ void __launch_bounds__(128) k_rap(Grid gin, Grid gout, Transfer tr,
   double out[27];
 #pragma unroll
   for (int s = 0; s < 27; ++s) out[s] = 0.0;
+  // Away from the ends of the direction the weights take one fixed pattern:
+  // wa = (1/2, 1, 1/2) and Pw[q] = e_0, (e_0 + e_1)/2, e_1, (e_1 + e_2)/2, e_2.
+  // There the products wa[a] Pw[a + d][D] are constants and only their 13
+  // nonzero terms (per pair of offsets in the other two directions) are
+  // formed; the general form below spends 4 multiply-adds per input value.
+  // Both add the same exact products (powers of two times S) in the same
+  // order, so they give identical results.
+  constexpr double kWa[3] = {0.5, 1.0, 0.5};
+  constexpr double kPw[5][3] = {{1.0, 0.0, 0.0}, {0.5, 0.5, 0.0}, {0.0, 1.0, 0.0},
+                                {0.0, 0.5, 0.5}, {0.0, 0.0, 1.0}};
+  bool regular = wa[0] == 0.5 && wa[2] == 0.5;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (wa[a] == 0.0) continue;
-    const int ii = DIM == 0 ? f + a - 1 : i;
-    const int jj = DIM == 1 ? f + a - 1 : j;
-    const int kk = DIM == 2 ? f + a - 1 : k;
-    const int64_t in = gidx(gin, ii, jj, kk);
+  for (int q = 0; q < 5; ++q)
 #pragma unroll
-    for (int s = 0; s < 27; ++s) {
-      const int di = s % 3, dj = (s / 3) % 3, dk = s / 9;  // 0..2
-      const int d = DIM == 0 ? di : (DIM == 1 ? dj : dk);
-      const double v = wa[a] * Sin[(int64_t)s * gin.total + in];
+    for (int D = 0; D < 3; ++D) regular = regular && Pw[q][D] == kPw[q][D];
+  if (regular) {
 #pragma unroll
-      for (int D = 0; D < 3; ++D) {
-        const int so = DIM == 0 ? D + 3 * dj + 9 * dk
-                                : (DIM == 1 ? di + 3 * D + 9 * dk : di + 3 * dj + 9 * D);
-        out[so] += v * Pw[a + d][D];
+    for (int a = 0; a < 3; ++a) {
+      const int ii = DIM == 0 ? f + a - 1 : i;
+      const int jj = DIM == 1 ? f + a - 1 : j;
+      const int kk = DIM == 2 ? f + a - 1 : k;
+      const int64_t in = gidx(gin, ii, jj, kk);
+#pragma unroll
+      for (int s = 0; s < 27; ++s) {
+        const int di = s % 3, dj = (s / 3) % 3, dk = s / 9;
+        const int d = DIM == 0 ? di : (DIM == 1 ? dj : dk);
+        const double v = Sin[(int64_t)s * gin.total + in];
+#pragma unroll
+        for (int D = 0; D < 3; ++D) {
+          const double w = kWa[a] * kPw[a + d][D];
+          if (w == 0.0) continue;
+          const int so = DIM == 0 ? D + 3 * dj + 9 * dk
+                                  : (DIM == 1 ? di + 3 * D + 9 * dk : di + 3 * dj + 9 * D);
+          out[so] = fma(v, w, out[so]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (wa[a] == 0.0) continue;
+      const int ii = DIM == 0 ? f + a - 1 : i;
+      const int jj = DIM == 1 ? f + a - 1 : j;
+      const int kk = DIM == 2 ? f + a - 1 : k;
+      const int64_t in = gidx(gin, ii, jj, kk);
+#pragma unroll
+      for (int s = 0; s < 27; ++s) {
+        const int di = s % 3, dj = (s / 3) % 3, dk = s / 9;  // 0..2
+        const int d = DIM == 0 ? di : (DIM == 1 ? dj : dk);
+        const double v = wa[a] * Sin[(int64_t)s * gin.total + in];
+#pragma unroll
+        for (int D = 0; D < 3; ++D) {
+          const int so = DIM == 0 ? D + 3 * dj + 9 * dk
+                                  : (DIM == 1 ? di + 3 * D + 9 * dk : di + 3 * dj + 9 * D);
+          out[so] += v * Pw[a + d][D];
+        }
       }
     }
   }

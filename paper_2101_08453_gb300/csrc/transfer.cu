@@ -108,6 +108,8 @@ __device__ __forceinline__ bool node_of_thread(const Grid& g, int& i, int& j, in
 }
 
 inline dim3 node_grid(const Grid& g) { return dim3((g.H + 31) / 32, (g.Ny + 3) / 4, 2 * g.Nz); }
+// one thread per column (i, j); blockIdx.z = parity of i
+inline dim3 column_grid(const Grid& g) { return dim3((g.H + 31) / 32, (g.Ny + 3) / 4, 2); }
 
 __global__ void k_update_mixed(Grid g, double* __restrict__ x, const float* __restrict__ e) {
   int i, j, k;
@@ -124,70 +126,142 @@ __device__ __forceinline__ void vcoarse(const Transfer& tr, int K, int& f, W& wm
   wp = (K < tr.Nzc - 1 && tr.kf[K + 1] - tr.kf[K] == 2) ? W(0.5) : W(0);
 }
 
-// f_c = P^T r at one coarse node: up to 3 x 3 x 3 fine residuals with the
-// interpolation weights (1 at the coarse node, 1/2 at the half nodes around
-// it), accumulated in the precision of the cycle (T).
-template <typename T>
-__global__ void k_restrict(Grid gf, Grid gc, Transfer tr, const T* __restrict__ r,
-                           T* __restrict__ fc) {
-  int I, J, K;
-  if (!node_of_thread(gc, I, J, K)) return;
-  const int64_t out = gidx(gc, I, J, K);
-  if (!is_free(gc, I, J, K)) { fc[out] = T(0); return; }
-  int fi, fj, fk;
-  T ax[3], ay[3], az[3];
-  hcoarse(tr.hx, gf.Nx, gc.Nx, I, fi, ax[0], ax[2]);
-  hcoarse(tr.hy, gf.Ny, gc.Ny, J, fj, ay[0], ay[2]);
-  vcoarse(tr, K, fk, az[0], az[2]);
-  ax[1] = ay[1] = az[1] = T(1);
-  T s = T(0);
+// f_c = P^T r (Eq. 7) over one coarse column (I, J), all K: each coarse node
+// gathers up to 3 x 3 x 3 fine residuals with the interpolation weights (1
+// at the coarse node, 1/2 at the half nodes around it), accumulated in the
+// precision of the cycle (T).  HX, HY: the level is coarsened in x, y.
+// Every tap is loaded without a branch (a tap outside the stencil of this
+// node reads a valid neighbour with weight 0, which adds an exact zero), and
+// layers go in chunks of U, so a thread has all loads of U nodes in flight.
+template <typename T, bool HX, bool HY>
+__global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
+                                                  const T* __restrict__ r, T* __restrict__ fc) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int I = 2 * h + (int)blockIdx.z;
+  if (I >= gc.Nx || J >= gc.Ny) return;
+  const int64_t own = (int64_t)J * gc.RP + (int64_t)(I & 1) * gc.H + (I >> 1);
+  if (I < 1 || I > gc.Nx - 2 || J < 1 || J > gc.Ny - 2) {
+    for (int K = 0; K < gc.Nz; ++K) fc[(int64_t)K * gc.PP + own] = T(0);
+    return;
+  }
+  constexpr int NA = HX ? 3 : 1, NB = HY ? 3 : 1;
+  int fi, fj;
+  T ax[3], ay[3];
+  hcoarse(HX ? 1 : 0, gf.Nx, gc.Nx, I, fi, ax[0], ax[2]);
+  hcoarse(HY ? 1 : 0, gf.Ny, gc.Ny, J, fj, ay[0], ay[2]);
+  ax[1] = ay[1] = T(1);
+  // in-layer offsets of the taps (fine columns fi-1..fi+1 are valid: I is interior)
+  int64_t hoff[NB][NA];
+  T wx[NA], wy[NB];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (az[c] == T(0)) continue;
+  for (int b = 0; b < NB; ++b) {
+    wy[b] = HY ? ay[b] : T(1);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      if (ay[b] == T(0)) continue;
-      T row = T(0);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (ax[a] == T(0)) continue;
-        row += ax[a] * r[gidx(gf, fi + a - 1, fj + b - 1, fk + c - 1)];
-      }
-      s += (ay[b] * az[c]) * row;
+    for (int a = 0; a < NA; ++a) {
+      const int ii = HX ? fi + a - 1 : fi, jj = HY ? fj + b - 1 : fj;
+      hoff[b][a] = (int64_t)jj * gf.RP + (int64_t)(ii & 1) * gf.H + (ii >> 1);
     }
   }
-  fc[out] = s;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) wx[a] = HX ? ax[a] : T(1);
+  const int Kend = gc.Nz - 1;  // the top layer is Dirichlet
+  constexpr int U = NA * NB >= 9 ? 1 : (NA * NB >= 3 ? 2 : 4);  // about 12 loads in flight
+  for (int K0 = 0; K0 < Kend; K0 += U) {
+    T v[U][3][NB][NA];
+    T az[U][3];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int K = min(K0 + u, Kend - 1);
+      int fk;
+      vcoarse(tr, K, fk, az[u][0], az[u][2]);
+      az[u][1] = T(1);
+      const int kl[3] = {az[u][0] != T(0) ? fk - 1 : fk, fk, az[u][2] != T(0) ? fk + 1 : fk};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T* rl = r + (int64_t)kl[c] * gf.PP;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int a = 0; a < NA; ++a) v[u][c][b][a] = rl[hoff[b][a]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      T out = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          T row = T(0);
+#pragma unroll
+          for (int a = 0; a < NA; ++a) row += wx[a] * v[u][c][b][a];
+          out += (wy[b] * az[u][c]) * row;
+        }
+      if (K0 + u < Kend) fc[(int64_t)(K0 + u) * gc.PP + own] = out;
+    }
+  }
+  fc[(int64_t)Kend * gc.PP + own] = T(0);
 }
 
-// x += P e_c at one fine node: up to 2 x 2 x 2 coarse values, in precision T.
-template <typename T>
-__global__ void k_prolong_add(Grid gf, Grid gc, Transfer tr, const T* __restrict__ ec,
-                              T* __restrict__ x) {
-  int i, j, k;
-  if (!node_of_thread(gf, i, j, k) || !is_free(gf, i, j, k)) return;
-  int ci[2], cj[2], ck[2];
-  T ax[2], ay[2], az[2];
-  hpair(tr.hx, gf.Nx, gc.Nx, i, ci[0], ax[0], ci[1], ax[1]);
-  hpair(tr.hy, gf.Ny, gc.Ny, j, cj[0], ay[0], cj[1], ay[1]);
-  ck[0] = tr.kc0[k]; ck[1] = tr.kc1[k]; az[0] = (T)tr.kw0[k]; az[1] = (T)tr.kw1[k];
-  T s = T(0);
+// x += P e_c (Eq. 7) over one fine column (i, j), all free k: up to 2 x 2 x 2
+// coarse values per node, in precision T; branch-free taps and chunks of U
+// layers as above.
+template <typename T, bool HX, bool HY>
+__global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer tr,
+                                                     const T* __restrict__ ec,
+                                                     T* __restrict__ x) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = 2 * h + (int)blockIdx.z;
+  if (i < 1 || i > gf.Nx - 2 || j < 1 || j > gf.Ny - 2) return;
+  constexpr int NA = HX ? 2 : 1, NB = HY ? 2 : 1;
+  int ci[2], cj[2];
+  T ax[2], ay[2];
+  hpair(HX ? 1 : 0, gf.Nx, gc.Nx, i, ci[0], ax[0], ci[1], ax[1]);
+  hpair(HY ? 1 : 0, gf.Ny, gc.Ny, j, cj[0], ay[0], cj[1], ay[1]);
+  int64_t hoff[NB][NA];
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    if (az[c] == T(0)) continue;
+  for (int b = 0; b < NB; ++b)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      if (ay[b] == T(0)) continue;
-      T row = T(0);
+    for (int a = 0; a < NA; ++a)
+      hoff[b][a] = (int64_t)cj[b] * gc.RP + (int64_t)(ci[a] & 1) * gc.H + (ci[a] >> 1);
+  const int64_t own = (int64_t)j * gf.RP + (int64_t)(i & 1) * gf.H + (i >> 1);
+  const int kend = gf.Nz - 1;  // free layers 0 .. Nz-2
+  constexpr int U = NA * NB >= 4 ? 2 : 4;
+  for (int k0 = 0; k0 < kend; k0 += U) {
+    T xv[U], ev[U][2][NB][NA], az[U][2];
 #pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        if (ax[a] == T(0)) continue;
-        row += ax[a] * ec[gidx(gc, ci[a], cj[b], ck[c])];
+    for (int u = 0; u < U; ++u) {
+      const int k = min(k0 + u, kend - 1);
+      xv[u] = x[(int64_t)k * gf.PP + own];
+      const int ck[2] = {tr.kc0[k], tr.kc1[k]};
+      az[u][0] = (T)tr.kw0[k];
+      az[u][1] = (T)tr.kw1[k];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T* el = ec + (int64_t)ck[c] * gc.PP;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int a = 0; a < NA; ++a) ev[u][c][b][a] = el[hoff[b][a]];
       }
-      s += (ay[b] * az[c]) * row;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      T sv = T(0);
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          T row = T(0);
+#pragma unroll
+          for (int a = 0; a < NA; ++a) row += (HX ? ax[a] : T(1)) * ev[u][c][b][a];
+          sv += ((HY ? ay[b] : T(1)) * az[u][c]) * row;
+        }
+      if (k0 + u < kend) x[(int64_t)(k0 + u) * gf.PP + own] = xv[u] + sv;
     }
   }
-  const int64_t o = gidx(gf, i, j, k);
-  x[o] += s;
 }
 
 }  // namespace
@@ -239,13 +313,23 @@ cudaError_t launch_update_mixed(const Grid& g, double* x, const float* e, cudaSt
 template <typename T>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const Transfer& tr, const T* r,
                             T* fc, cudaStream_t st) {
-  k_restrict<T><<<node_grid(gc), dim3(32, 4), 0, st>>>(gf, gc, tr, r, fc); count_launches(1);
+  const dim3 grd = column_grid(gc), blk(32, 4);
+  if (tr.hx && tr.hy) k_restrict<T, true, true><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+  else if (tr.hx) k_restrict<T, true, false><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+  else if (tr.hy) k_restrict<T, false, true><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+  else k_restrict<T, false, false><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+  count_launches(1);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const Transfer& tr, const T* ec,
                                T* x, cudaStream_t st) {
-  k_prolong_add<T><<<node_grid(gf), dim3(32, 4), 0, st>>>(gf, gc, tr, ec, x); count_launches(1);
+  const dim3 grd = column_grid(gf), blk(32, 4);
+  if (tr.hx && tr.hy) k_prolong_add<T, true, true><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+  else if (tr.hx) k_prolong_add<T, true, false><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+  else if (tr.hy) k_prolong_add<T, false, true><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+  else k_prolong_add<T, false, false><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+  count_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_restrict<double>(const Grid&, const Grid&, const Transfer&,

@@ -391,3 +391,9 @@ def test_element_arithmetic(torch, arith, tol, name):
     if name not in _lam_ref:
         _lam_ref[name] = oracle.solve(c)
     assert rel(lam.cpu().numpy().ravel(), _lam_ref[name]) <= 1e-10
+    # recovery at the element centers (Eq. 7) from the same multiplier:
+    # float pairs and float64 agree with the oracle element by element
+    lam_h = lam.cpu().numpy().ravel()
+    u = plan.recover(u0, lam, m.AT_CENTERS).cpu().numpy()
+    u_ref = oracle.recover(c, lam_h, where=m.AT_CENTERS)
+    assert np.abs(u - u_ref).max() <= tol * np.abs(u_ref).max()
