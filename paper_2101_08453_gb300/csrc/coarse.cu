@@ -27,7 +27,7 @@ __global__ void k_dense_gather(Grid g, const double* __restrict__ C, int n,
   const int ii = i + s % 3 - 1, jj = j + (s / 3) % 3 - 1, kk = k + s / 9 - 1;
   if (!is_free(g, ii, jj, kk)) return;
   const int col = (kk * n2 + (jj - 1)) * n1 + (ii - 1);
-  A[(int64_t)row * n + col] = C[(int64_t)s * g.total + gidx(g, i, j, k)];
+  A[(int64_t)row * n + col] = C[cidx(gidx(g, i, j, k), s)];
 }
 
 __global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, int n, int p) {

@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
       if (!is_free(g, in, jn, kn)) continue;
       int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
               9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-      C[(int64_t)s * g.total + row] += (n >= m) ? Ke[m][n] : Ke[n][m];
+      C[cidx(row, s)] += (n >= m) ? Ke[m][n] : Ke[n][m];
     }
   }
 }

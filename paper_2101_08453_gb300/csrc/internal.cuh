@@ -8,14 +8,15 @@
 // warp over consecutive same-group columns reads the stencil planes with
 // unit stride instead of stride 2.
 //
-// A level's float64 operator is stored as 28 planes of that layout: plane
-// s = (di+1) + 3(dj+1) + 9(dk+1) (s = 13 the diagonal) holds K_FF(n, n+d),
-// plane 27 holds 1/K(n, n).  Rows and columns of fixed (Dirichlet) nodes
-// are zero, so the planes hold exactly the free block K_FF of Eq. 5.
-// The float32 copy is tiled instead: the 28 coefficients of 32 consecutive
-// nodes of a half row are one contiguous 3584-byte tile (coefficient s of
-// node b at ((b >> 5) * 28 + s) * 32 + (b & 31)), so a warp stepping
-// through a layer reads one contiguous block rather than 28 planes.
+// A level's operator holds 28 coefficients per node: s = (di+1) + 3(dj+1)
+// + 9(dk+1) (s = 13 the diagonal) holds K_FF(n, n+d), s = 27 holds
+// 1/K(n, n).  Rows and columns of fixed (Dirichlet) nodes are zero, so the
+// coefficients are exactly the free block K_FF of Eq. 5.  Both the float64
+// operator and its float32 copy are tiled: the 28 coefficients of 32
+// consecutive nodes of a half row are one contiguous tile (coefficient s of
+// node b at ((b >> 5) * 28 + s) * 32 + (b & 31); 7168 or 3584 bytes), so a
+// warp stepping through a layer reads one contiguous block rather than 28
+// separate streams.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -58,12 +59,18 @@ __host__ __device__ inline int64_t gidx(const Grid& g, int i, int j, int k) {
   return (int64_t)k * g.PP + (int64_t)j * g.RP + (int64_t)(i & 1) * g.H + (i >> 1);
 }
 
-// coefficient s of node b (split-layout index): planar float64, tiled float32
-__device__ __forceinline__ double coef(const double* C, int64_t total, int64_t b, int s) {
-  return C[(int64_t)s * total + b];
+// Operator storage, float64 and float32 alike: tiles of 32 consecutive
+// split-layout nodes, each tile holding the kPlanes coefficients of its 32
+// nodes plane after plane (32 values per plane), so one warp's rows are
+// one contiguous block.  cidx = position of coefficient s of node b.
+__host__ __device__ constexpr int64_t cidx(int64_t b, int s) {
+  return ((b >> 5) * kPlanes + s) * 32 + (b & 31);
+}
+__device__ __forceinline__ double coef(const double* C, int64_t, int64_t b, int s) {
+  return C[cidx(b, s)];
 }
 __device__ __forceinline__ float coef(const float* C, int64_t, int64_t b, int s) {
-  return C[((b >> 5) * kPlanes + s) * 32 + (b & 31)];
+  return C[cidx(b, s)];
 }
 
 __host__ __device__ inline bool is_free(const Grid& g, int i, int j, int k) {

@@ -47,14 +47,21 @@ __global__ void k_stencil_export(Grid g, const T* __restrict__ C, double* __rest
   for (int s = 0; s < 27; ++s) out[s * n + o] = (double)coef(C, g.total, id, s);
 }
 
-// planar float64 operator -> tiled float32 copy (one thread per node index b)
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ t, int64_t total) {
+// float64 operator -> float32 copy in the same tiled order: n = kPlanes x
+// total values, 2 per thread and turn (16-byte loads, 8-byte stores)
+__global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ t, int64_t n2) {
   int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
-  for (; b < total; b += st) {
-    float* dst = t + (b >> 5) * (kPlanes * 32) + (b & 31);
-#pragma unroll 4
-    for (int s = 0; s < kPlanes; ++s) dst[s * 32] = (float)a[(int64_t)s * total + b];
+  for (; b + 3 * st < n2; b += 4 * st) {
+    double2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = a[b + q * st];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[b + q * st] = make_float2((float)v[q].x, (float)v[q].y);
+  }
+  for (; b < n2; b += st) {
+    const double2 v = a[b];
+    t[b] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -66,11 +73,11 @@ __global__ void k_finalize(Grid g, double* __restrict__ C, int* flag) {
 #pragma unroll
   for (int s = 0; s < 27; ++s) {
     int di = s % 3 - 1, dj = (s / 3) % 3 - 1, dk = s / 9 - 1;
-    if (!fr || !is_free(g, i + di, j + dj, k + dk)) C[s * g.total + id] = 0.0;
+    if (!fr || !is_free(g, i + di, j + dj, k + dk)) C[cidx(id, s)] = 0.0;
   }
-  double d = C[kDiag * g.total + id];
+  double d = C[cidx(id, kDiag)];
   if (fr && !(d > 0.0)) atomicOr(flag, 2);
-  C[kInvDiag * g.total + id] = fr ? 1.0 / d : 0.0;
+  C[cidx(id, kInvDiag)] = fr ? 1.0 / d : 0.0;
 }
 
 constexpr int kRedThreads = 128;
@@ -147,8 +154,9 @@ template cudaError_t launch_stencil_export<double>(const Grid&, const double*, d
 template cudaError_t launch_stencil_export<float>(const Grid&, const float*, double*, cudaStream_t);
 
 cudaError_t launch_stencil_to_f32(const Grid& g, const double* C64, float* C32, cudaStream_t st) {
-  int blocks = (int)std::min<int64_t>((g.total + 255) / 256, 152 * 16);
-  k_to_f32<<<blocks, 256, 0, st>>>(C64, C32, g.total); count_launches(1);
+  const int64_t n2 = (int64_t)kPlanes * g.total / 2;  // total is a multiple of 64
+  int blocks = (int)std::min<int64_t>((n2 + 255) / 256, 152 * 16);
+  k_to_f32<<<blocks, 256, 0, st>>>((const double2*)C64, (float2*)C32, n2); count_launches(1);
   return cudaGetLastError();
 }
 

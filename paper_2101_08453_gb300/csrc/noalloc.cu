@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128) k_residual_norm_noalloc(Grid g, const dou
       const double fk = f[(int64_t)k * lay + col[4]];
       double acc = fk;
 #pragma unroll
-      for (int s = 0; s < 27; ++s) acc -= C[s * g.total + b] * w[s / 9][s % 9];
+      for (int s = 0; s < 27; ++s) acc -= C[cidx(b, s)] * w[s / 9][s % 9];
       sf += fk * fk;
       sr += acc * acc;
 #pragma unroll

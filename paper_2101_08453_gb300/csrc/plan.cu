@@ -189,8 +189,9 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
     if (outs.size() >= 3) tmpB = std::max(tmpB, outs[1]);
   }
   p->off_tmp = off;
-  p->tmp_bytes = align256(27 * tmpA * 8);
-  off = align256(off + p->tmp_bytes + 27 * tmpB * 8);
+  // stage outputs in the tiled operator layout (28 slots per node, 27 used)
+  p->tmp_bytes = align256(kPlanes * tmpA * 8);
+  off = align256(off + p->tmp_bytes + kPlanes * tmpB * 8);
   p->n_coarse = (int)nc;
   p->off_dense = off; off = align256(off + 2 * (size_t)nc * nc * 8);
   p->off_cfree = off; off = align256(off + (size_t)nc * 4);

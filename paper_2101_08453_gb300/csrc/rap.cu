@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(128) k_rap(Grid gin, Grid gout, Transfer tr,
       for (int s = 0; s < 27; ++s) {
         const int di = s % 3, dj = (s / 3) % 3, dk = s / 9;
         const int d = DIM == 0 ? di : (DIM == 1 ? dj : dk);
-        const double v = Sin[(int64_t)s * gin.total + in];
+        const double v = Sin[cidx(in, s)];
 #pragma unroll
         for (int D = 0; D < 3; ++D) {
           const double w = kWa[a] * kPw[a + d][D];
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(128) k_rap(Grid gin, Grid gout, Transfer tr,
       for (int s = 0; s < 27; ++s) {
         const int di = s % 3, dj = (s / 3) % 3, dk = s / 9;  // 0..2
         const int d = DIM == 0 ? di : (DIM == 1 ? dj : dk);
-        const double v = wa[a] * Sin[(int64_t)s * gin.total + in];
+        const double v = wa[a] * Sin[cidx(in, s)];
 #pragma unroll
         for (int D = 0; D < 3; ++D) {
           const int so = DIM == 0 ? D + 3 * dj + 9 * dk
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128) k_rap(Grid gin, Grid gout, Transfer tr,
   }
   const int64_t o = gidx(gout, i, j, k);
 #pragma unroll
-  for (int s = 0; s < 27; ++s) Sout[(int64_t)s * gout.total + o] = out[s];
+  for (int s = 0; s < 27; ++s) Sout[cidx(o, s)] = out[s];
 }
 
 }  // namespace
