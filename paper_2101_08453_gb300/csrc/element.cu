@@ -371,19 +371,29 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
 #pragma unroll
     for (int m = 0; m <= n; ++m) Ke[m][n] = Num<R>::to(col[m]);
   }
-  // scatter: row of local node m gets Ke[m][n] at offset (n - m)
+  // scatter: row of local node m gets Ke[m][n] at offset (n - m).  The 8
+  // targets of a row are distinct, so their loads are issued together
+  // before the stores (a plain += per target would wait for each round trip).
+  bool fr[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n)
+    fr[n] = is_free(g, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1));
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
-    if (!is_free(g, im, jm, km)) continue;
-    int64_t row = gidx(g, im, jm, km);
+    if (!fr[m]) continue;
+    const int64_t row = gidx(g, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1));
+    double cur[8];
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      int in = i + (n & 1), jn = j + ((n >> 1) & 1), kn = k + ((n >> 2) & 1);
-      if (!is_free(g, in, jn, kn)) continue;
-      int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
-              9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-      C[cidx(row, s)] += (n >= m) ? Ke[m][n] : Ke[n][m];
+      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+      cur[n] = fr[n] ? C[cidx(row, s)] : 0.0;
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+      if (fr[n]) C[cidx(row, s)] = cur[n] + ((n >= m) ? Ke[m][n] : Ke[n][m]);
     }
   }
 }
@@ -537,12 +547,18 @@ __global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, in
     }
     weak_div_modal<R>(G, vg, fe);
   }
+  // the 8 node rows are distinct: all loads first, then the stores
+  double cur[8];
+  bool fr[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
-    if (!is_free(g, im, jm, km)) continue;
-    f[gidx(g, im, jm, km)] -= fe[m];
+    const int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
+    fr[m] = is_free(g, im, jm, km);
+    cur[m] = fr[m] ? f[gidx(g, im, jm, km)] : 0.0;
   }
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+    if (fr[m]) f[gidx(g, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] = cur[m] - fe[m];
 }
 
 // float64 -> (hi, lo) float pairs, n values, split in integer arithmetic
