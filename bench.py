@@ -411,6 +411,7 @@ def main():
 
     X, Y, Z, U0, U0N = (torch.from_numpy(a).to(dev) for a in (case.X, case.Y, case.Z, case.u0, u0n_np))
     plan = m.Plan.for_case(case, precision=prec)
+    plan_cpc = plan.options.cycles_per_check
     lam = torch.zeros(plan.node_shape, dtype=torch.float64, device=dev)
     u_c = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)
     u_w = torch.empty_like(u_c)
@@ -655,7 +656,8 @@ def main():
                    "rtol": RTOL, "levels": plan_levels if False else None,
                    "l2": "inputs larger than L2 (X, Y, Z, u0, u0' = %.1f GB resident)" % (
                        9 * n_nodes * 8 / 1e9),
-                   "replicas": world},
+                   "replicas": world,
+                   "cycles_per_check": (plan_cpc or (2 if prec == m.PREC_MIXED else 1))},
         "gpu_launches": int(launches),
         "cycles_per_step": {"cold": cycles[-1][0], "warm": cycles[-1][1]},
         "rel_res": {"cold": cycles[-1][2], "warm": cycles[-1][3]},

@@ -122,6 +122,15 @@ typedef struct {
      rate on GB300; MCWIND_ARITH_F64: float64.  Sums into the stencil and the
      load vector, and everything after assembly, are float64 either way. */
   int element_arith;
+  /* V-cycles between two convergence checks, 1..8; 0 (default) = 2 with
+     MCWIND_PREC_MIXED, 1 with MCWIND_PREC_F64.  In mixed precision the
+     cycles of one check run back to back on the float32 correction (the
+     second from the first one's result, as in the plain multigrid
+     iteration) before the float64 update and residual, which are computed
+     once per check.  Solves stop at a check, so the cycle count is a
+     multiple of this (or max_cycles).  Ignored with MCWIND_ACCEL_CG (one
+     cycle per iteration). */
+  int cycles_per_check;
 } mcwind_options;
 
 typedef struct {
@@ -130,7 +139,9 @@ typedef struct {
   double norm_f;         /* ||f_F||_2, f the load vector of Eq. 5 */
   double rel_res;        /* final ||f_F - K_FF lambda_F||_2 / ||f_F||_2 */
   double rate;           /* geometric mean residual reduction per cycle, from cycle 3 on */
-  double res_hist[MCWIND_HIST]; /* relative residual before cycle 1 (index 0), then after each */
+  double res_hist[MCWIND_HIST]; /* relative residual before cycle 1 (index 0), then after each;
+                                   between two checks (cycles_per_check > 1) the entries are
+                                   the geometric interpolation of the checked values */
 } mcwind_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -297,7 +308,8 @@ int mcwind_batch_create(int n, const mcwind_plan* plans, void* workspace, mcwind
 /* Solve every domain d: u0[d], lambda[d] as in mcwind_solve.  Iterates until
  * every domain is at or below rtol or max_cycles; a domain stops iterating
  * once it reaches rtol (one cached graph per set of still-active domains), so
- * each domain gets exactly the result of its own mcwind_solve.  stats: host,
+ * each domain gets exactly the result of its own mcwind_solve (checks every
+ * cycles_per_check cycles of the first plan; give the plans one setting).  stats: host,
  * n entries, may be NULL.  Returns OK, ENOTCONV (some domain above rtol),
  * ENONFINITE, EINVAL. */
 int mcwind_batch_solve(mcwind_batch batch, const double* const* u0, double* const* lambda,

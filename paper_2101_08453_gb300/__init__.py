@@ -50,7 +50,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("rhs_quad", ctypes.c_int),
                 ("post_reverse", ctypes.c_int), ("accel", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("u0_at", ctypes.c_int),
-                ("element_arith", ctypes.c_int)]
+                ("element_arith", ctypes.c_int), ("cycles_per_check", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -234,15 +234,32 @@ int outer_residual(mcwind_plan p, cudaStream_t st) {
   return MCWIND_OK;
 }
 
-int one_cycle(mcwind_plan p, cudaStream_t st) {
+// V-cycles between two convergence checks (the option, or its default)
+int check_every(mcwind_plan p) {
+  if (p->opt.cycles_per_check > 0) return p->opt.cycles_per_check;
+  return p->opt.precision == MCWIND_PREC_MIXED ? 2 : 1;
+}
+
+// n V-cycles, then the float64 residual and its norm (one check).  Mixed
+// precision: the cycles iterate on the float32 correction (the first from
+// the zero the outer residual left), then x += e once.
+int iteration(mcwind_plan p, cudaStream_t st, int n) {
   if (p->opt.precision == MCWIND_PREC_F64) {
-    CKR(vcycle<double>(p, 0, st));
+    for (int q = 0; q < n; ++q) CKR(vcycle<double>(p, 0, st));
   } else {
-    CKR(vcycle<float>(p, 0, st, true));  // the outer residual zeroed the correction
+    for (int q = 0; q < n; ++q) CKR(vcycle<float>(p, 0, st, q == 0));
     PROF(MCWIND_K_UPDATE);
     CK(launch_update_mixed(p->lv[0].g, lv64(p, 0).x, lv32(p, 0).x, st));
   }
   return outer_residual(p, st);
+}
+
+// res_hist entries c0+1 .. c1-1 between two checks: geometric interpolation
+void fill_between(double* h, int c0, int c1) {
+  for (int q = c0 + 1; q < c1; ++q)
+    h[q] = (h[c0] > 0.0 && h[c1] > 0.0)
+               ? h[c0] * std::pow(h[c1] / h[c0], (double)(q - c0) / (c1 - c0))
+               : h[c1];
 }
 
 // Run one solver iteration (body(p, stream)) on st: replayed from a graph
@@ -593,11 +610,19 @@ static int solve_impl(mcwind_plan p, const double* u0, const double* f_given, do
   } else {
     S.res_hist[0] = std::sqrt(h[1]) / nf;
     int c = 0;
+    const int kc = check_every(p);
     while (S.res_hist[c] > rtol && c < max_cycles) {
-      CKR(run_iteration(p, st, one_cycle));
+      const int n = std::min(kc, max_cycles - c);
+      if (n == kc)
+        CKR(run_iteration(p, st, [kc](mcwind_plan q, cudaStream_t s2) -> int {
+          return iteration(q, s2, kc);
+        }));
+      else
+        CKR(iteration(p, st, n));  // a shorter last step runs outside the graph
       CKR(read_scalars(p, h + 1, 1, 1, st));
-      ++c;
-      S.res_hist[c] = std::sqrt(h[1]) / nf;
+      S.res_hist[c + n] = std::sqrt(h[1]) / nf;
+      fill_between(S.res_hist, c, c + n);
+      c += n;
       if (!std::isfinite(S.res_hist[c])) break;
     }
     S.cycles = c;
@@ -905,7 +930,9 @@ void batch_clear_graphs(mcwind_batch b) {
 }
 
 // one iteration of the active domains, from the graph cached for that set
-int batch_iteration(mcwind_batch b, const std::string& active, cudaStream_t st) {
+// n V-cycles and a check on the active domains, replayed from the graph of
+// that active set and n
+int batch_iteration(mcwind_batch b, const std::string& active, int n, cudaStream_t st) {
   bool stale = false;
   for (size_t d = 0; d < b->plans.size() && !stale; ++d)
     stale = b->ws_at_capture[d] != b->plans[d]->ws || b->tuning_at_capture[d] != tuning_key(b->plans[d]);
@@ -916,13 +943,14 @@ int batch_iteration(mcwind_batch b, const std::string& active, cudaStream_t st) 
       b->tuning_at_capture[d] = tuning_key(b->plans[d]);
     }
   }
-  auto it = b->graphs.find(active);
+  const std::string key = active + "#" + std::to_string(n);
+  auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     const long long n0 = mcwind_launch_count();
-    const int rc = fork_join(b, b->cap, active, [b](int d, cudaStream_t s) -> int {
+    const int rc = fork_join(b, b->cap, active, [b, n](int d, cudaStream_t s) -> int {
       mcwind_plan p = b->plans[d];
-      CKR(one_cycle(p, s));
+      CKR(iteration(p, s, n));
       CK(cudaMemcpyAsync(b->dres + 2 * d + 1, scal(p) + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
       return MCWIND_OK;
     });
@@ -939,7 +967,7 @@ int batch_iteration(mcwind_batch b, const std::string& active, cudaStream_t st) 
     CK(ei);
     const long long nl = mcwind_launch_count() - n0;
     count_launches(-(int)nl);
-    it = b->graphs.emplace(active, std::make_pair(exec, nl)).first;
+    it = b->graphs.emplace(key, std::make_pair(exec, nl)).first;
   }
   CK(cudaGraphLaunch(it->second.first, st));
   count_launches((int)it->second.second);
@@ -1053,15 +1081,19 @@ extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, doubl
   int c = 0;
   std::string active(n, '0');
   for (int d = 0; d < n; ++d) active[d] = S[d].cycles < 0 ? '1' : '0';
+  const int kc = check_every(b->plans[0]);  // the first domain's setting holds for all
   while (!all_done && c < max_cycles) {
-    CKR(batch_iteration(b, active, st));
+    const int nc = std::min(kc, max_cycles - c);
+    CKR(batch_iteration(b, active, nc, st));
     CK(cudaMemcpyAsync(h.data(), b->dres, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    ++c;
+    const int c0 = c;
+    c += nc;
     all_done = true;
     for (int d = 0; d < n; ++d) {
       if (S[d].cycles >= 0) continue;
       S[d].res_hist[c] = nf[d] > 0.0 ? std::sqrt(h[2 * d + 1]) / nf[d] : 0.0;
+      fill_between(S[d].res_hist, c0, c);
       if (S[d].res_hist[c] <= rtol || !std::isfinite(S[d].res_hist[c])) {
         S[d].cycles = c;
         active[d] = '0';

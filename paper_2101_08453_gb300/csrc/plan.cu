@@ -108,6 +108,7 @@ extern "C" void mcwind_default_options(mcwind_options* o) {
   o->use_graphs = 1;
   o->u0_at = MCWIND_U0_NODES;
   o->element_arith = MCWIND_ARITH_DFLOAT;
+  o->cycles_per_check = 0;
 }
 
 extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], double h1,
@@ -140,6 +141,7 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   if (o.use_graphs != 0 && o.use_graphs != 1) return MCWIND_EINVAL;
   if (o.u0_at != MCWIND_U0_NODES && o.u0_at != MCWIND_U0_CENTERS) return MCWIND_EINVAL;
   if (o.element_arith != MCWIND_ARITH_F64 && o.element_arith != MCWIND_ARITH_DFLOAT) return MCWIND_EINVAL;
+  if (o.cycles_per_check < 0 || o.cycles_per_check > 8) return MCWIND_EINVAL;
 
   std::vector<PlanLevel> H = hierarchy(nx, ny, nz, a, h1, h3, o.coarsen_rule, o.coarsest_max);
   if (H.empty() || !H.back().kmap.empty()) return MCWIND_EINVAL;

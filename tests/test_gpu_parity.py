@@ -397,3 +397,31 @@ def test_element_arithmetic(torch, arith, tol, name):
     u = plan.recover(u0, lam, m.AT_CENTERS).cpu().numpy()
     u_ref = oracle.recover(c, lam_h, where=m.AT_CENTERS)
     assert np.abs(u - u_ref).max() <= tol * np.abs(u_ref).max()
+
+
+@pytest.mark.parametrize("name", ["hill64", "aniso"])
+def test_cycles_per_check(torch, name):
+    """Mixed precision with 1, 2 and 3 V-cycles between float64 checks: each
+    reaches the oracle's solution; the cycle count is a multiple of the
+    spacing, and the history between two checks is their geometric
+    interpolation."""
+    c = CASES[name]
+    if name not in _lam_ref:
+        _lam_ref[name] = oracle.solve(c)
+    counts = {}
+    for k in (1, 2, 3):
+        _, plan, (X, Y, Z, u0), _ = setup(torch, name, precision=m.PREC_MIXED,
+                                          coarsest_max=1024, cycles_per_check=k)
+        lam, st = plan.solve(u0, rtol=1e-12, max_cycles=120)
+        assert st.status == m.MCWIND_OK and st.rel_res <= 1e-12, (k, st.history()[-3:])
+        assert st.cycles % k == 0
+        assert rel(lam.cpu().numpy().ravel(), _lam_ref[name]) <= 1e-10
+        h = st.history()
+        for q in range(k, st.cycles + 1, k):
+            for r in range(1, k):
+                want = h[q - k] * (h[q] / h[q - k]) ** (r / k)
+                assert abs(h[q - k + r] - want) <= 1e-12 * want
+        counts[k] = st.cycles
+    # the float64 check does not change the cycle itself: the spacing costs at
+    # most the cycles up to the next check
+    assert counts[2] <= counts[1] + 2 and counts[3] <= counts[1] + 3, counts
