@@ -149,6 +149,23 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+# whole-job aggregate over the ranks (replicas: no data-path collective)
+
+def job_totals(dist, seconds, work, device):
+    """Slowest rank's time and the summed work of all ranks (one replica of
+    the domain per rank).  dist is None for one process; otherwise an
+    initialized torch.distributed (nccl on the GPUs, gloo in the tests)."""
+    if dist is None:
+        return float(seconds), float(work)
+    import torch
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work)], device=device, dtype=torch.float64)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
+# --------------------------------------------------------------------------
 # clocks during the timed region
 
 class ClockSampler:
@@ -417,23 +434,42 @@ def main():
     u_w = torch.empty_like(u_c)
     stream = torch.cuda.current_stream()
 
+    copy_stream = torch.cuda.Stream(device=dev)
+    ev_u0n = torch.cuda.Event()
+    ev_uc = torch.cuda.Event()
+
     def step(inputs=None, outputs=None, ev=None):
+        # With host buffers, the next time step's wind is copied in on a copy
+        # stream while the grid is assembled and the first wind solved, and
+        # the first wind field is copied out while the second is solved.
         if inputs is not None:
-            for dst, src in zip((X, Y, Z, U0, U0N), inputs):
+            for dst, src in zip((X, Y, Z, U0), inputs[:4]):
                 dst.copy_(src, non_blocking=True)
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                U0N.copy_(inputs[4], non_blocking=True)
+                ev_u0n.record(copy_stream)
         if ev: ev[0].record()
         plan.assemble(X, Y, Z)
         if ev: ev[1].record()
         _, s1 = m.mcwind_solve(plan.handle, U0, lam, RTOL, 100, 0)
         if ev: ev[2].record()
         m.mcwind_recover(plan.handle, U0, lam, u_c)
+        if outputs is not None:
+            ev_uc.record(stream)
+            copy_stream.wait_event(ev_uc)
+            with torch.cuda.stream(copy_stream):
+                outputs[0].copy_(u_c, non_blocking=True)
+        if inputs is not None:
+            stream.wait_event(ev_u0n)
         _, s2 = m.mcwind_solve(plan.handle, U0N, lam, RTOL, 100, m.WARM)
         if ev: ev[3].record()
         m.mcwind_recover(plan.handle, U0N, lam, u_w)
         if ev: ev[4].record()
         if outputs is not None:
-            outputs[0].copy_(u_c, non_blocking=True)
             outputs[1].copy_(u_w, non_blocking=True)
+        if inputs is not None or outputs is not None:
+            stream.wait_stream(copy_stream)
         if s1.status != 0 or s2.status != 0:
             raise RuntimeError(f"solve did not converge: {s1.status} {s2.status}")
         return s1, s2
@@ -467,14 +503,7 @@ def main():
     work = n_free * sum(c[0] + c[1] for c in cycles)
     phases = np.array([[phase_ev[s][q].elapsed_time(phase_ev[s][q + 1]) for q in range(4)]
                        for s in range(args.steps)])
-    if dist is not None:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wsum = torch.tensor([float(work)], device=dev, dtype=torch.float64)
-        dist.all_reduce(wsum, op=dist.ReduceOp.SUM)
-        t_dev, work_all = float(t), float(wsum)
-    else:
-        work_all = float(work)
+    t_dev, work_all = job_totals(dist, t_dev, work, dev)
     value = work_all / t_dev
 
     # one more step without the profiler (solver iterations replayed from graphs)
@@ -503,12 +532,7 @@ def main():
             ework += n_free * (s1.cycles + s2.cycles)
         a1.record()
         barrier()
-        te = a0.elapsed_time(a1) / 1e3
-        if dist is not None:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t)
-            ework *= world
+        te, ework = job_totals(dist, a0.elapsed_time(a1) / 1e3, ework, dev)
         h2d = sum(p.numel() * 8 for p in pin)
         d2h = sum(o.numel() * 8 for o in outs)
         e2e = {"value": ework / te, "unit": UNIT, "h2d_bytes_per_step": h2d,

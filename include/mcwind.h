@@ -119,8 +119,13 @@ typedef struct {
   /* Arithmetic of the 2x2x2-Gauss element kernels (stiffness and load
      vector).  MCWIND_ARITH_DFLOAT (default): pairs of floats (about 48
      significant bits) on the float pipe, which issues 61 times the float64
-     rate on GB300; MCWIND_ARITH_F64: float64.  Sums into the stencil and the
-     load vector, and everything after assembly, are float64 either way. */
+     rate on GB300, for the element values and for their sums into the
+     stencil and the load vector (each entry is rounded to float64 once, by
+     the last element that adds to it); MCWIND_ARITH_F64: float64 throughout.
+     The Galerkin products of the coarser levels sum in float pairs either
+     way (their interpolation weights make every product exact); the stored
+     operators and the solve are float64 (float32 inside the float64
+     refinement of MCWIND_PREC_MIXED). */
   int element_arith;
   /* V-cycles between two convergence checks, 1..8; 0 (default) = 2 with
      MCWIND_PREC_MIXED, 1 with MCWIND_PREC_F64.  In mixed precision the

@@ -31,12 +31,45 @@ __device__ __forceinline__ dflt df_of(double x) {
 }
 __device__ __forceinline__ dflt df_of(float x) { return {x, 0.0f}; }
 
+// The rare cases of the integer conversions below go through the double
+// pipe in functions of their own: a call is a real branch, so the compiler
+// cannot turn the rare path into predicated instructions that every call
+// would issue.
+static __host__ __device__ __noinline__ float2 split_by_conversion(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+static __host__ __device__ __noinline__ double pair_sum_by_conversion(float hi, float lo) {
+  return (double)hi + (double)lo;
+}
+static __host__ __device__ __noinline__ float float_by_conversion(double x) { return (float)x; }
+
+// (float)r for |r| < 2^29, rounded to nearest even, on the float pipe (the
+// int-to-float conversion instruction shares the double pipe's issue rate
+// on GB300): the two halves h = r >> 14 and l = r & 0x3FFF are read exactly
+// off the 1.5 * 2^23 bias, and h * 2^14 + l is rounded once by the FMA.
+__host__ __device__ inline float float_of_i29(int r) {
+  const int h = r >> 14, l = r & 0x3FFF;
+#ifdef __CUDA_ARCH__
+  const float fh = __int_as_float(0x4B400000 + h) - 12582912.0f;
+  const float fl = __int_as_float(0x4B400000 + l) - 12582912.0f;
+  return __fmaf_rn(fh, 16384.0f, fl);
+#else
+  const int bh = 0x4B400000 + h, bl = 0x4B400000 + l;
+  float fh, fl;
+  __builtin_memcpy(&fh, &bh, 4);
+  __builtin_memcpy(&fl, &bl, 4);
+  return __builtin_fmaf(fh - 12582912.0f, 16384.0f, fl - 12582912.0f);
+#endif
+}
+
 // The same split of a double taken apart in integer arithmetic, without the
 // double pipe: hi = the leading 24 significand bits rounded to nearest
 // (halfway cases away from zero), lo = the remaining 29 bits, signed, rounded
 // to a float and scaled by the exponent.  hi + lo = x to within
-// 2^-48 |x|, |lo| <= ulp(hi)/2.  Values outside [2^-70, 2^100] in
-// magnitude, zero, infinities and NaN take the conversion path of df_of.
+// 2^-48 |x|, |lo| <= ulp(hi)/2.  Zero gives (+-0, 0); other values outside
+// [2^-70, 2^100] in magnitude, infinities and NaN take the conversion path
+// of df_of.
 __host__ __device__ inline float2 split_bits(double x) {
 #ifdef __CUDA_ARCH__
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
@@ -46,10 +79,16 @@ __host__ __device__ inline float2 split_bits(double x) {
 #endif
   const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
   const int e = (int)((h32 >> 20) & 0x7FFu);
-  if (e < 1023 - 70 || e > 1023 + 100) {
-    const float h = (float)x;
-    return make_float2(h, (float)(x - (double)h));
+  if ((u << 1) == 0ull) {
+#ifdef __CUDA_ARCH__
+    return make_float2(__uint_as_float(h32), 0.0f);
+#else
+    float z;
+    __builtin_memcpy(&z, &h32, 4);
+    return make_float2(z, 0.0f);
+#endif
   }
+  if (e < 1023 - 70 || e > 1023 + 100) return split_by_conversion(x);
   const unsigned sign = h32 & 0x80000000u;
   // magnitude bits of the truncated float: exponent rebased, top 23 fraction bits
   unsigned hb = ((unsigned)(e - 1023 + 127) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
@@ -62,18 +101,109 @@ __host__ __device__ inline float2 split_bits(double x) {
   const unsigned sb = (unsigned)(e - 948) << 23;
 #ifdef __CUDA_ARCH__
   const float scale = __uint_as_float(sb);
-  const float lo = __int2float_rn(r) * scale;
+  const float lo = float_of_i29(r) * scale;
   const float hi = __uint_as_float(hb | sign);
 #else
   float scale, hi;
   __builtin_memcpy(&scale, &sb, 4);
   const unsigned hs = hb | sign;
   __builtin_memcpy(&hi, &hs, 4);
-  const float lo = (float)r * scale;
+  const float lo = float_of_i29(r) * scale;
 #endif
   return make_float2(hi, sign ? -lo : lo);
 }
 __device__ __forceinline__ double to_double(dflt a) { return (double)a.hi + (double)a.lo; }
+
+// hi + lo rounded to the nearest double (ties to even), the value to_double
+// gives, formed in integer arithmetic so that it takes no double-pipe
+// instruction.  The pair must be normalized (|lo| <= ulp(hi)/2, as every
+// sum and product below leaves it).  |hi| as a double is its bit pattern
+// with the exponent rebased and the 23 fraction bits moved up by 29; lo is
+// then a whole number k of units of the double's last place in hi's binade
+// (|k| <= 2^28), added to the magnitude's bit pattern.  That addition never
+// carries into the exponent; it borrows from it only when hi is a power of
+// two and lo lowers the magnitude, and then k is taken in the units of the
+// binade below.  Zeros give the sum's zero; hi outside [2^-74, 2^128), infinities
+// and NaN take the double-pipe path.
+__host__ __device__ inline double pair_to_double(float hi, float lo) {
+#ifdef __CUDA_ARCH__
+  const unsigned uh = __float_as_uint(hi);
+#else
+  unsigned uh;
+  __builtin_memcpy(&uh, &hi, 4);
+#endif
+  const int eh = (int)((uh >> 23) & 0xFFu);
+  if ((uh << 1) == 0u && lo == 0.0f) {  // zero, negative only if both parts are -0
+#ifdef __CUDA_ARCH__
+    const unsigned ul = __float_as_uint(lo);
+    return __longlong_as_double((long long)((unsigned long long)(uh & ul) << 32));
+#else
+    unsigned ul;
+    __builtin_memcpy(&ul, &lo, 4);
+    const unsigned long long zb = (unsigned long long)(uh & ul) << 32;
+    double z;
+    __builtin_memcpy(&z, &zb, 8);
+    return z;
+#endif
+  }
+  if (eh < 53 || eh > 254) return pair_sum_by_conversion(hi, lo);
+  const unsigned sign = uh & 0x80000000u, mh = uh & 0x7FFFFFu;
+  unsigned long long mag = ((unsigned long long)(((unsigned)(eh + 896) << 20) | (mh >> 3)) << 32) |
+                           ((unsigned long long)(mh & 7u) << 29);
+  const float l = sign ? -lo : lo;  // lo's share of the magnitude
+  // 2^(52 - E) (or 2^(53 - E) for the binade below), E = eh - 127
+  const unsigned sb = (unsigned)((mh == 0u && l < 0.0f) ? 307 - eh : 306 - eh) << 23;
+#ifdef __CUDA_ARCH__
+  const int k = __float2int_rn(l * __uint_as_float(sb));
+  return __longlong_as_double((long long)((mag + (unsigned long long)(long long)k) |
+                                          ((unsigned long long)sign << 32)));
+#else
+  float scale;
+  __builtin_memcpy(&scale, &sb, 4);
+  const int k = (int)__builtin_nearbyintf(l * scale);
+  const unsigned long long bits = (mag + (unsigned long long)(long long)k) | ((unsigned long long)sign << 32);
+  double out;
+  __builtin_memcpy(&out, &bits, 8);
+  return out;
+#endif
+}
+__host__ __device__ inline double pair_to_double(float2 v) { return pair_to_double(v.x, v.y); }
+
+// (float)x, rounded to nearest with ties to even as the conversion does, in
+// integer arithmetic: the 23 fraction bits kept are rounded on the 29 below
+// them (a carry may roll into the exponent, up to infinity).  Zero keeps
+// its sign; results that would be subnormal or overflow before rounding,
+// infinities and NaN take the conversion.
+__host__ __device__ inline float float_of_bits(double x) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  __builtin_memcpy(&u, &x, 8);
+#endif
+  const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
+  const unsigned sign = h32 & 0x80000000u;
+  const int e = (int)((h32 >> 20) & 0x7FFu);
+  unsigned fb;
+  if (e == 0 && (h32 & 0xFFFFFu) == 0u && l32 == 0u) {
+    fb = sign;
+  } else if (e < 1023 - 126 || e > 1023 + 127) {
+    return float_by_conversion(x);
+  } else {
+    const unsigned top = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);  // 23 fraction bits
+    const unsigned rem = l32 & 0x1FFFFFFFu;
+    fb = ((unsigned)(e - 1023 + 127) << 23) | top;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (top & 1u))) fb += 1u;
+    fb |= sign;
+  }
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(fb);
+#else
+  float out;
+  __builtin_memcpy(&out, &fb, 4);
+  return out;
+#endif
+}
 
 // Sum with error at most about 2^-48 (|a| + |b|): the high parts are added
 // exactly (two-sum), the low parts in float, then renormalized.

@@ -147,6 +147,30 @@ __device__ __forceinline__ bool elem_of_thread(int nx, int ny, int nz, int cls, 
   return i < nx && j < ny && k < nz;
 }
 
+// The 8 element-parity classes are assembled in the order 0..7.  Among the
+// elements that hold both local nodes m and n of element (i, j, k) (m == n:
+// the elements around node m), the first to be assembled has parity 0, and
+// the last parity 1, along every axis where the two nodes share their
+// coordinate and the element on the other side of that coordinate exists;
+// along the other axes all of them have this element's parity.
+__device__ __forceinline__ bool class_is(int nx, int ny, int nz, int i, int j, int k, int m, int n,
+                                         int want) {
+  bool ok = true;
+  if (((m ^ n) & 1) == 0) {
+    const int o = (m & 1) ? i + 1 : i - 1;
+    if (o >= 0 && o < nx && (i & 1) != want) ok = false;
+  }
+  if (((m ^ n) & 2) == 0) {
+    const int o = (m & 2) ? j + 1 : j - 1;
+    if (o >= 0 && o < ny && (j & 1) != want) ok = false;
+  }
+  if (((m ^ n) & 4) == 0) {
+    const int o = (m & 4) ? k + 1 : k - 1;
+    if (o >= 0 && o < nz && (k & 1) != want) ok = false;
+  }
+  return ok;
+}
+
 __host__ __device__ constexpr int popc3(int q) { return (q & 1) + ((q >> 1) & 1) + ((q >> 2) & 1); }
 // index of the symmetric 3x3 component (a, b) in (00, 01, 02, 11, 12, 22)
 __host__ __device__ constexpr int sym6(int a, int b) {
@@ -169,7 +193,10 @@ struct Num<double> {
 };
 template <>
 struct Num<dflt> {
-  __device__ static dflt from(double v) { return df_of(v); }
+  __device__ static dflt from(double v) {
+    const float2 t = split_bits(v);
+    return {t.x, t.y};
+  }
   __device__ static double to(dflt v) { return to_double(v); }
   __device__ static dflt rcp(dflt v) { return reciprocal(v); }
   __device__ static bool pos(dflt v) { return positive(v); }
@@ -361,7 +388,7 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
     }
 #pragma unroll
   for (int S = 1; S < 8; ++S) wht8_t<R>(Kt[S]);
-  double Ke[8][8];
+  R Ke[8][8];  // m <= n
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
     R col[8];
@@ -369,7 +396,7 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
     for (int S = 0; S < 8; ++S) col[S] = Kt[S][n];
     wht8_t<R>(col);
 #pragma unroll
-    for (int m = 0; m <= n; ++m) Ke[m][n] = Num<R>::to(col[m]);
+    for (int m = 0; m <= n; ++m) Ke[m][n] = col[m];
   }
   // scatter: row of local node m gets Ke[m][n] at offset (n - m).  The 8
   // targets of a row are distinct, so their loads are issued together
@@ -382,18 +409,45 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
   for (int m = 0; m < 8; ++m) {
     if (!fr[m]) continue;
     const int64_t row = gidx(g, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1));
-    double cur[8];
+    if constexpr (__is_same(R, dflt)) {
+      // Float pairs: an entry holds the (hi, lo) pair of its partial sum in
+      // its 8 bytes until the last element class that touches it stores the
+      // sum as a double; the first class writes without reading.  No
+      // double-pipe instruction.
+      float2* C2 = reinterpret_cast<float2*>(C);
+      float2 cur[8];
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
-                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-      cur[n] = fr[n] ? C[cidx(row, s)] : 0.0;
-    }
+      for (int n = 0; n < 8; ++n) {
+        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+        cur[n] = (fr[n] && !class_is(nx, ny, nz, i, j, k, m, n, 0)) ? C2[cidx(row, s)]
+                                                                     : make_float2(0.0f, 0.0f);
+      }
 #pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
-                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-      if (fr[n]) C[cidx(row, s)] = cur[n] + ((n >= m) ? Ke[m][n] : Ke[n][m]);
+      for (int n = 0; n < 8; ++n) {
+        if (!fr[n]) continue;
+        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+        const dflt v = dflt{cur[n].x, cur[n].y} + ((n >= m) ? Ke[m][n] : Ke[n][m]);
+        if (class_is(nx, ny, nz, i, j, k, m, n, 1))
+          C[cidx(row, s)] = pair_to_double(v.hi, v.lo);
+        else
+          C2[cidx(row, s)] = make_float2(v.hi, v.lo);
+      }
+    } else {
+      double cur[8];
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+        cur[n] = fr[n] ? C[cidx(row, s)] : 0.0;
+      }
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+        if (fr[n]) C[cidx(row, s)] = cur[n] + ((n >= m) ? Ke[m][n] : Ke[n][m]);
+      }
     }
   }
 }
@@ -402,7 +456,7 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
 // the Gauss points: with w^_q = sum_g sigma_q(g) w_g the modal load is
 // f^[S] = s^(|S|-1) sum_{a in S} w^_{S\a}[a] and out = 1/8 H f^.
 template <typename R>
-__device__ __forceinline__ void weak_div_modal(const GeoT<R>& G, const R vg[8][3], double out[8]) {
+__device__ __forceinline__ void weak_div_modal_t(const GeoT<R>& G, const R vg[8][3], R fv[8]) {
   R Jc[3][4][3];
   jac_columns<R>(G, Jc);
   R wh[8][3];
@@ -426,7 +480,6 @@ __device__ __forceinline__ void weak_div_modal(const GeoT<R>& G, const R vg[8][3
     for (int q = 0; q < 8; ++q) wh[q][r] = (popc3(q) & 1) ? -t[q] : t[q];
   }
   // f~[S] = (-1)^|S| f^[S] / 8, then out = W f~
-  R fv[8];
   fv[0] = Num<R>::from(0.0);
 #pragma unroll
   for (int S = 1; S < 8; ++S) {
@@ -442,6 +495,12 @@ __device__ __forceinline__ void weak_div_modal(const GeoT<R>& G, const R vg[8][3
     fv[S] = v * Num<R>::from(spow(e - 1) * ((e & 1) ? -1.0 : 1.0) * 0.125);
   }
   wht8_t<R>(fv);
+}
+
+template <typename R>
+__device__ __forceinline__ void weak_div_modal(const GeoT<R>& G, const R vg[8][3], double out[8]) {
+  R fv[8];
+  weak_div_modal_t<R>(G, vg, fv);
 #pragma unroll
   for (int m = 0; m < 8; ++m) out[m] = Num<R>::to(fv[m]);
 }
@@ -487,25 +546,29 @@ __device__ __forceinline__ void interp_gauss_modal(const R ue[8][3], R vg[8][3])
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, int nz,
+// QUAD: bit 0 = one-point rule at the center, bit 1 = u0 given at the
+// element centers (a compile-time choice, so that each kernel carries only
+// its own code).
+template <typename R, int QUAD>
+__global__ void __launch_bounds__(128, 3) k_assemble_rhs(Grid g, int nx, int ny, int nz,
                                                       const double* __restrict__ X,
                                                       const double* __restrict__ Y,
                                                       const double* __restrict__ Z,
                                                       const float2* __restrict__ xyz2,
                                                       const double* __restrict__ u0,
-                                                      const float2* __restrict__ u2, int quad,
+                                                      const float2* __restrict__ u2,
                                                       double* __restrict__ f, int cls) {
+  constexpr int quad = QUAD;
   int i, j, k;
   if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
-  double fe[8];
+  R fe[8];
   const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
   const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-  if (quad & 1) {
+  if constexpr ((quad & 1) != 0) {
     Geo G;
     load_geo(X, Y, Z, nx + 1, ny + 1, i, j, k, G);
     double v[3];
-    if (quad & 2) {
+    if constexpr ((quad & 2) != 0) {
       v[0] = u0[e]; v[1] = u0[NE + e]; v[2] = u0[2 * NE + e];
     } else {
       double ue[8][3];
@@ -518,12 +581,15 @@ __global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, in
         v[d] = 0.125 * sum;
       }
     }
-    weak_div_center(G, v, fe);
+    double fd[8];
+    weak_div_center(G, v, fd);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) fe[m] = Num<R>::from(fd[m]);
   } else {
     GeoT<R> G;
     load_geo_t<R>(X, Y, Z, xyz2, N, nx + 1, ny + 1, i, j, k, G);
     R vg[8][3];
-    if (quad & 2) {
+    if constexpr ((quad & 2) != 0) {
       // u0 given at the element centers: constant over the element
       const R c0 = Num<R>::from(u0[e]), c1 = Num<R>::from(u0[NE + e]), c2 = Num<R>::from(u0[2 * NE + e]);
 #pragma unroll
@@ -545,20 +611,24 @@ __global__ void __launch_bounds__(128) k_assemble_rhs(Grid g, int nx, int ny, in
       }
       interp_gauss_modal<R>(ue, vg);
     }
-    weak_div_modal<R>(G, vg, fe);
+    weak_div_modal_t<R>(G, vg, fe);
   }
-  // the 8 node rows are distinct: all loads first, then the stores
+  // the 8 node rows are distinct: all loads first, then the stores.  (Float
+  // pairs for these 8 sums, as in the stiffness scatter, measured slower:
+  // the double adds here are few.)
   double cur[8];
   bool fr[8];
+  int64_t at[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
     fr[m] = is_free(g, im, jm, km);
-    cur[m] = fr[m] ? f[gidx(g, im, jm, km)] : 0.0;
+    at[m] = gidx(g, im, jm, km);
+    cur[m] = fr[m] ? f[at[m]] : 0.0;
   }
 #pragma unroll
   for (int m = 0; m < 8; ++m)
-    if (fr[m]) f[gidx(g, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1))] = cur[m] - fe[m];
+    if (fr[m]) f[at[m]] = cur[m] - Num<R>::to(fe[m]);
 }
 
 // float64 -> (hi, lo) float pairs, n values, split in integer arithmetic
@@ -916,10 +986,20 @@ cudaError_t launch_assemble_rhs(const Grid& g, int nx, int ny, int nz, const dou
   for (int cls = 0; cls < 8; ++cls) {
     dim3 grd = elem_grid(nx, ny, nz, cls, blk);
     if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
-    if (dfloat)
-      k_assemble_rhs<dflt><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, u0, u2, quad, f, cls);
-    else
-      k_assemble_rhs<double><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, u0, u2, quad, f, cls);
+#define MCW_RHS(Q)                                                                            \
+  do {                                                                                        \
+    if (dfloat)                                                                               \
+      k_assemble_rhs<dflt, Q><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, u0, u2, f, cls); \
+    else                                                                                      \
+      k_assemble_rhs<double, Q><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, u0, u2, f, cls); \
+  } while (0)
+    switch (quad & 3) {
+      case 0: MCW_RHS(0); break;
+      case 1: MCW_RHS(1); break;
+      case 2: MCW_RHS(2); break;
+      default: MCW_RHS(3); break;
+    }
+#undef MCW_RHS
     count_launches(1);
   }
   return cudaGetLastError();

@@ -1,4 +1,5 @@
 // Layout conversion, stencil finalization and deterministic reductions.
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace mcw {
@@ -48,7 +49,8 @@ __global__ void k_stencil_export(Grid g, const T* __restrict__ C, double* __rest
 }
 
 // float64 operator -> float32 copy in the same tiled order: n = kPlanes x
-// total values, 2 per thread and turn (16-byte loads, 8-byte stores)
+// total values, 2 per thread and turn (16-byte loads, 8-byte stores); the
+// rounding is done in integer arithmetic (float_of_bits), off the double pipe
 __global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ t, int64_t n2) {
   int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
@@ -57,11 +59,11 @@ __global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ t, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[q] = a[b + q * st];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) t[b + q * st] = make_float2((float)v[q].x, (float)v[q].y);
+    for (int q = 0; q < 4; ++q) t[b + q * st] = make_float2(float_of_bits(v[q].x), float_of_bits(v[q].y));
   }
   for (; b < n2; b += st) {
     const double2 v = a[b];
-    t[b] = make_float2((float)v.x, (float)v.y);
+    t[b] = make_float2(float_of_bits(v.x), float_of_bits(v.y));
   }
 }
 
