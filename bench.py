@@ -37,9 +37,12 @@ CELLS = (3000, 3000, 15)
 RTOL = 1e-8
 SAMPLE_W = 160       # CPU baseline / reference window (cells per side)
 SAMPLE_I0, SAMPLE_J0 = 1420, 1420
-# FP32-pipe thread instructions per element of the element kernels in float-pair
-# arithmetic (the default), counted by ncu (sm__inst_executed_pipe_fma x 32 / elements)
-# on one element-parity launch of the 600x600x15 case (720000 elements)
+# Float-pair arithmetic per element of the modal element kernels (the default):
+# the FP32-pipe thread instructions of their fully unrolled form, counted by ncu
+# (sm__inst_executed_pipe_fma x 32 / elements) on one element-parity launch of the
+# 600x600x15 case (720000 elements).  The kernels that run keep their loops rolled
+# over shared memory and issue some more (selects, addressing); this count is the
+# arithmetic the method needs, the `alu` roofline's numerator.
 FP32_OPS_STIFFNESS = 14198.0
 FP32_OPS_LOAD = 8308.0
 # FP32 pipe: 128 lanes per SM x 152 SMs x 2.07 GHz maximum SM clock

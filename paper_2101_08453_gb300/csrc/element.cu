@@ -17,8 +17,12 @@
 //   K_e      = 1/64 H K^ H^T,   H[n][S] = eps_n^S = (-1)^|S| W[n][S],
 // W the 8-point Walsh-Hadamard matrix: two fast transforms instead of the
 // 8 x 36 three-term products of the nodal form.  The load vector is done the
-// same way with w_g = adj(J_g) u0(g).  Every Gauss loop is unrolled, so the
-// shape-function values are compile-time constants.
+// same way with w_g = adj(J_g) u0(g).  The shape-function values at the
+// Gauss points are compile-time constants (sign patterns and powers of
+// 1/sqrt(3)).  The float64 kernels unroll every loop; the float-pair kernels
+// (the default) keep the Gauss points and transforms in loops over
+// per-thread shared memory, because their unrolled code is too long for the
+// instruction cache.
 //
 // Assembly scatters element contributions in 8 launches, one per element
 // parity class (i mod 2, j mod 2, k mod 2): elements of one class share no
@@ -197,7 +201,7 @@ struct Num<dflt> {
     const float2 t = split_bits(v);
     return {t.x, t.y};
   }
-  __device__ static double to(dflt v) { return to_double(v); }
+  __device__ static double to(dflt v) { return pair_to_double(v.hi, v.lo); }
   __device__ static dflt rcp(dflt v) { return reciprocal(v); }
   __device__ static bool pos(dflt v) { return positive(v); }
 };
@@ -306,6 +310,8 @@ __device__ __forceinline__ void wht8(double x[8]) {
       }
 }
 
+// Stiffness in arithmetic R, fully unrolled; instantiated for float64 (the
+// float-pair form is k_assemble_stencil_df below).
 template <typename R>
 __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int ny, int nz,
                                                           const double* __restrict__ X,
@@ -409,45 +415,190 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
   for (int m = 0; m < 8; ++m) {
     if (!fr[m]) continue;
     const int64_t row = gidx(g, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1));
-    if constexpr (__is_same(R, dflt)) {
-      // Float pairs: an entry holds the (hi, lo) pair of its partial sum in
-      // its 8 bytes until the last element class that touches it stores the
-      // sum as a double; the first class writes without reading.  No
-      // double-pipe instruction.
-      float2* C2 = reinterpret_cast<float2*>(C);
-      float2 cur[8];
+    double cur[8];
 #pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
-                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-        cur[n] = (fr[n] && !class_is(nx, ny, nz, i, j, k, m, n, 0)) ? C2[cidx(row, s)]
-                                                                     : make_float2(0.0f, 0.0f);
-      }
+    for (int n = 0; n < 8; ++n) {
+      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+      cur[n] = fr[n] ? C[cidx(row, s)] : 0.0;
+    }
 #pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        if (!fr[n]) continue;
-        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
-                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-        const dflt v = dflt{cur[n].x, cur[n].y} + ((n >= m) ? Ke[m][n] : Ke[n][m]);
-        if (class_is(nx, ny, nz, i, j, k, m, n, 1))
-          C[cidx(row, s)] = pair_to_double(v.hi, v.lo);
-        else
-          C2[cidx(row, s)] = make_float2(v.hi, v.lo);
-      }
-    } else {
-      double cur[8];
+    for (int n = 0; n < 8; ++n) {
+      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+      if (fr[n]) C[cidx(row, s)] = cur[n] + ((n >= m) ? Ke[m][n] : Ke[n][m]);
+    }
+  }
+}
+
+// The float-pair stiffness kernel with its repeated work in loops.  Fully
+// unrolled, the per-element code is about 16 k instructions executed once
+// each, and fetching them bounds the kernel (ncu: most stalls wait for an
+// instruction).  Here the Gauss points, the 6 sign sums, the 15 transforms
+// of the 8 x 8 modal matrix and the 8 scatter rows are loops, and the values
+// they index by the loop counter live in shared memory (64 float pairs per
+// thread, each thread touching only its own column: no barrier).
+constexpr int kAsmThreads = 128;
+constexpr int kAsmSlots = 64;
+
+__device__ __forceinline__ dflt sel4(const dflt& v0, const dflt& v1, const dflt& v2, const dflt& v3,
+                                     int q) {
+  const dflt a = (q & 1) ? v1 : v0, b = (q & 1) ? v3 : v2;
+  return (q & 2) ? b : a;
+}
+
+__global__ void __launch_bounds__(kAsmThreads, 3) k_assemble_stencil_df(
+    Grid g, int nx, int ny, int nz, const float2* __restrict__ xyz2, float2 d0, float2 d1,
+    float2 d2, double* __restrict__ C, int* flag, int cls) {
+  extern __shared__ float2 sm_asm[];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  float2* my = sm_asm + tid;  // slot q of this thread: my[q * kAsmThreads]
+  int i, j, k;
+  if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
+  const dflt D[3] = {{d0.x, d0.y}, {d1.x, d1.y}, {d2.x, d2.y}};
+  dflt Jc[3][4][3];
+  {
+    GeoT<dflt> G;
+    load_geo_t<dflt>(nullptr, nullptr, nullptr, xyz2, (int64_t)(nx + 1) * (ny + 1) * (nz + 1),
+                     nx + 1, ny + 1, i, j, k, G);
+    jac_columns<dflt>(G, Jc);
+  }
+  // C_g = adj D adj^T / det at Gauss point gp -> slots gp * 6 + c
+  bool bad = false;
+#pragma unroll 1
+  for (int gp = 0; gp < 8; ++gp) {
+    const int gx = gp & 1, gy = (gp >> 1) & 1, gz = gp >> 2;
+    const int q0 = gy + 2 * gz, q1 = gx + 2 * gz, q2 = gx + 2 * gy;
+    dflt J[3][3], adj[3][3];
 #pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
-                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-        cur[n] = fr[n] ? C[cidx(row, s)] : 0.0;
-      }
+    for (int d = 0; d < 3; ++d) {
+      J[d][0] = sel4(Jc[0][0][d], Jc[0][1][d], Jc[0][2][d], Jc[0][3][d], q0);
+      J[d][1] = sel4(Jc[1][0][d], Jc[1][1][d], Jc[1][2][d], Jc[1][3][d], q1);
+      J[d][2] = sel4(Jc[2][0][d], Jc[2][1][d], Jc[2][2][d], Jc[2][3][d], q2);
+    }
+    const dflt det = adjugate_t<dflt>(J, adj);
+    bad |= !positive(det);
+    const dflt inv = reciprocal(det);
+    dflt aD[3][3];
 #pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
-                      9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
-        if (fr[n]) C[cidx(row, s)] = cur[n] + ((n >= m) ? Ke[m][n] : Ke[n][m]);
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) aD[r][t] = adj[r][t] * D[t];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int t = r; t < 3; ++t) {
+        const dflt v = (aD[r][0] * adj[t][0] + aD[r][1] * adj[t][1] + aD[r][2] * adj[t][2]) * inv;
+        my[(gp * 6 + sym6(r, t)) * kAsmThreads] = make_float2(v.hi, v.lo);
       }
+  }
+  if (bad) atomicOr(flag, 1);
+  // sign sums over the Gauss points, in place: sum_g sigma_q(g) C_g = (-1)^|q| (W C)[q]
+#pragma unroll 1
+  for (int c = 0; c < 6; ++c) {
+    dflt v[8];
+#pragma unroll
+    for (int gp = 0; gp < 8; ++gp) {
+      const float2 t = my[(gp * 6 + c) * kAsmThreads];
+      v[gp] = dflt{t.x, t.y};
+    }
+    wht8_t<dflt>(v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const dflt t = (popc3(q) & 1) ? -v[q] : v[q];
+      my[(q * 6 + c) * kAsmThreads] = make_float2(t.hi, t.lo);
+    }
+  }
+  // K~ = D K^ D / 64 (D[S] = (-1)^|S|), upper triangle; row and column 0 vanish
+  dflt Kt[28];
+#pragma unroll
+  for (int S = 1; S < 8; ++S)
+#pragma unroll
+    for (int T = S; T < 8; ++T) {
+      dflt v = dflt{0.0f, 0.0f};
+      bool first = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (!((S >> a) & 1)) continue;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if (!((T >> b) & 1)) continue;
+          const float2 w = my[(((S & ~(1 << a)) ^ (T & ~(1 << b))) * 6 + sym6(a, b)) * kAsmThreads];
+          v = first ? dflt{w.x, w.y} : v + dflt{w.x, w.y};
+          first = false;
+        }
+      }
+      const int e = popc3(S) + popc3(T);
+      // upper-triangle index of (S, T), 1 <= S <= T <= 7
+      Kt[(S - 1) * (16 - S) / 2 + (T - S)] =
+          v * Num<dflt>::from(spow(e - 2) * ((e & 1) ? -1.0 : 1.0) / 64.0);
+    }
+  // the full symmetric 8 x 8 matrix, slot S * 8 + T
+#pragma unroll
+  for (int S = 0; S < 8; ++S)
+#pragma unroll
+    for (int T = 0; T < 8; ++T) {
+      const int lo = S < T ? S : T, hi = S < T ? T : S;
+      const dflt v = (lo == 0) ? dflt{0.0f, 0.0f} : Kt[(lo - 1) * (16 - lo) / 2 + (hi - lo)];
+      my[(S * 8 + T) * kAsmThreads] = make_float2(v.hi, v.lo);
+    }
+  // K_e = W K~ W: transform the rows (row 0 stays zero), then the columns
+#pragma unroll 1
+  for (int S = 1; S < 8; ++S) {
+    dflt r[8];
+#pragma unroll
+    for (int T = 0; T < 8; ++T) {
+      const float2 t = my[(S * 8 + T) * kAsmThreads];
+      r[T] = dflt{t.x, t.y};
+    }
+    wht8_t<dflt>(r);
+#pragma unroll
+    for (int T = 0; T < 8; ++T) my[(S * 8 + T) * kAsmThreads] = make_float2(r[T].hi, r[T].lo);
+  }
+#pragma unroll 1
+  for (int n = 0; n < 8; ++n) {
+    dflt col[8];
+#pragma unroll
+    for (int S = 0; S < 8; ++S) {
+      const float2 t = my[(S * 8 + n) * kAsmThreads];
+      col[S] = dflt{t.x, t.y};
+    }
+    wht8_t<dflt>(col);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) my[(m * 8 + n) * kAsmThreads] = make_float2(col[m].hi, col[m].lo);
+  }
+  // scatter: row of local node m gets K_e[m][n] at offset (n - m), summed in
+  // float pairs until the last element class that touches the entry stores
+  // it as a double (the first class writes without reading)
+  float2* C2 = reinterpret_cast<float2*>(C);
+  unsigned freem = 0u;
+#pragma unroll
+  for (int n = 0; n < 8; ++n)
+    if (is_free(g, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1))) freem |= 1u << n;
+#pragma unroll 1
+  for (int m = 0; m < 8; ++m) {
+    if (!((freem >> m) & 1u)) continue;
+    const int64_t row = gidx(g, i + (m & 1), j + ((m >> 1) & 1), k + ((m >> 2) & 1));
+    float2 cur[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+      cur[n] = (((freem >> n) & 1u) && !class_is(nx, ny, nz, i, j, k, m, n, 0))
+                   ? C2[cidx(row, s)]
+                   : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      if (!((freem >> n) & 1u)) continue;
+      const int s = ((n & 1) - (m & 1) + 1) + 3 * (((n >> 1) & 1) - ((m >> 1) & 1) + 1) +
+                    9 * (((n >> 2) & 1) - ((m >> 2) & 1) + 1);
+      const float2 ke = my[((m < n ? m : n) * 8 + (m < n ? n : m)) * kAsmThreads];
+      const dflt v = dflt{cur[n].x, cur[n].y} + dflt{ke.x, ke.y};
+      if (class_is(nx, ny, nz, i, j, k, m, n, 1))
+        C[cidx(row, s)] = pair_to_double(v.hi, v.lo);
+      else
+        C2[cidx(row, s)] = make_float2(v.hi, v.lo);
     }
   }
 }
@@ -544,6 +695,118 @@ __device__ __forceinline__ void interp_gauss_modal(const R ue[8][3], R vg[8][3])
 #pragma unroll
     for (int gp = 0; gp < 8; ++gp) vg[gp][d] = t[gp];
   }
+}
+
+// The float-pair load vector (2x2x2 Gauss, nodal u0: the default mode)
+// with its Gauss-point loop and sign sums rolled like the stiffness kernel;
+// u0 at the Gauss points and adj(J_g) u0(g) live in shared memory (24 float
+// pairs per thread, own column only: no barrier).
+constexpr int kRhsSlots = 24;
+
+__global__ void __launch_bounds__(kAsmThreads, 4) k_assemble_rhs_df(
+    Grid g, int nx, int ny, int nz, const float2* __restrict__ xyz2, const float2* __restrict__ u2,
+    double* __restrict__ f, int cls) {
+  extern __shared__ float2 sm_rhs[];
+  float2* my = sm_rhs + (threadIdx.y * blockDim.x + threadIdx.x);  // slot q: my[q * kAsmThreads]
+  int i, j, k;
+  if (!elem_of_thread(nx, ny, nz, cls, i, j, k)) return;
+  const int64_t N = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  // u0 at the Gauss points, 1/8 W (s^|S| (W u)), component d -> slots gp * 3 + d
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dflt t[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const float2 v =
+          u2[d * N + sidx(nx + 1, ny + 1, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1))];
+      t[n] = dflt{v.x, v.y};
+    }
+    wht8_t<dflt>(t);
+#pragma unroll
+    for (int S = 0; S < 8; ++S) t[S] = t[S] * Num<dflt>::from(spow(popc3(S)) * 0.125);
+    wht8_t<dflt>(t);
+#pragma unroll
+    for (int gp = 0; gp < 8; ++gp) my[(gp * 3 + d) * kAsmThreads] = make_float2(t[gp].hi, t[gp].lo);
+  }
+  dflt Jc[3][4][3];
+  {
+    GeoT<dflt> G;
+    load_geo_t<dflt>(nullptr, nullptr, nullptr, xyz2, N, nx + 1, ny + 1, i, j, k, G);
+    jac_columns<dflt>(G, Jc);
+  }
+  // w_g = adj(J_g) u0(g), written over u0(g)
+#pragma unroll 1
+  for (int gp = 0; gp < 8; ++gp) {
+    const int gx = gp & 1, gy = (gp >> 1) & 1, gz = gp >> 2;
+    const int q0 = gy + 2 * gz, q1 = gx + 2 * gz, q2 = gx + 2 * gy;
+    dflt J[3][3], adj[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      J[d][0] = sel4(Jc[0][0][d], Jc[0][1][d], Jc[0][2][d], Jc[0][3][d], q0);
+      J[d][1] = sel4(Jc[1][0][d], Jc[1][1][d], Jc[1][2][d], Jc[1][3][d], q1);
+      J[d][2] = sel4(Jc[2][0][d], Jc[2][1][d], Jc[2][2][d], Jc[2][3][d], q2);
+    }
+    adjugate_t<dflt>(J, adj);
+    dflt v[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float2 t = my[(gp * 3 + d) * kAsmThreads];
+      v[d] = dflt{t.x, t.y};
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const dflt w = adj[r][0] * v[0] + adj[r][1] * v[1] + adj[r][2] * v[2];
+      my[(gp * 3 + r) * kAsmThreads] = make_float2(w.hi, w.lo);
+    }
+  }
+  // sign sums over the Gauss points, in place: (-1)^|q| (W w)[q]
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+    dflt t[8];
+#pragma unroll
+    for (int gp = 0; gp < 8; ++gp) {
+      const float2 v = my[(gp * 3 + r) * kAsmThreads];
+      t[gp] = dflt{v.x, v.y};
+    }
+    wht8_t<dflt>(t);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const dflt v = (popc3(q) & 1) ? -t[q] : t[q];
+      my[(q * 3 + r) * kAsmThreads] = make_float2(v.hi, v.lo);
+    }
+  }
+  // f~[S] = (-1)^|S| f^[S] / 8, then the nodal load = W f~
+  dflt fv[8];
+  fv[0] = dflt{0.0f, 0.0f};
+#pragma unroll
+  for (int S = 1; S < 8; ++S) {
+    dflt v = dflt{0.0f, 0.0f};
+    bool first = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if ((S >> a) & 1) {
+        const float2 t = my[((S & ~(1 << a)) * 3 + a) * kAsmThreads];
+        v = first ? dflt{t.x, t.y} : v + dflt{t.x, t.y};
+        first = false;
+      }
+    const int e = popc3(S);
+    fv[S] = v * Num<dflt>::from(spow(e - 1) * ((e & 1) ? -1.0 : 1.0) * 0.125);
+  }
+  wht8_t<dflt>(fv);
+  // the 8 node rows are distinct: all loads first, then the stores
+  double cur[8];
+  bool fr[8];
+  int64_t at[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int im = i + (m & 1), jm = j + ((m >> 1) & 1), km = k + ((m >> 2) & 1);
+    fr[m] = is_free(g, im, jm, km);
+    at[m] = gidx(g, im, jm, km);
+    cur[m] = fr[m] ? f[at[m]] : 0.0;
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m)
+    if (fr[m]) f[at[m]] = cur[m] - pair_to_double(fv[m].hi, fv[m].lo);
 }
 
 // QUAD: bit 0 = one-point rule at the center, bit 1 = u0 given at the
@@ -736,7 +999,7 @@ __global__ void __launch_bounds__(128) k_recover_center_df(int nx, int ny, int n
                                                            const float2* __restrict__ u2,
                                                            const double* __restrict__ u0c,
                                                            const float2* __restrict__ lam2,
-                                                           double d0, double d1, double d2,
+                                                           float2 d0, float2 d1, float2 d2,
                                                            double* __restrict__ u) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -773,12 +1036,15 @@ __global__ void __launch_bounds__(128) k_recover_center_df(int nx, int ny, int n
     gr[r] = acc * 0.125f;
   }
   const int64_t NE = (int64_t)nx * ny * nz, e = ((int64_t)k * ny + j) * nx + i;
-  const double dd[3] = {d0, d1, d2};
+  const dflt dd[3] = {{d0.x, d0.y}, {d1.x, d1.y}, {d2.x, d2.y}};
+  // no double-pipe instruction: inputs split and the output formed in
+  // integer arithmetic
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     dflt uc;
     if (u0c) {
-      uc = df_of(u0c[d * NE + e]);
+      const float2 v = split_bits(u0c[d * NE + e]);
+      uc = dflt{v.x, v.y};
     } else {
       float2 v = u2[d * N + id[0]];
       uc = dflt{v.x, v.y};
@@ -790,7 +1056,8 @@ __global__ void __launch_bounds__(128) k_recover_center_df(int nx, int ny, int n
       uc = uc * 0.125f;
     }
     const dflt gd = (adj[0][d] * gr[0] + adj[1][d] * gr[1] + adj[2][d] * gr[2]) * inv;
-    u[(int64_t)d * NE + e] = to_double(uc + gd * df_of(dd[d]));
+    const dflt ud = uc + gd * dd[d];
+    u[(int64_t)d * NE + e] = pair_to_double(ud.hi, ud.lo);
   }
 }
 
@@ -965,12 +1232,19 @@ cudaError_t launch_assemble_stencil(const Grid& g, int nx, int ny, int nz, const
                                     const double* a, double* C, int* flag, int dfloat,
                                     cudaStream_t st) {
   dim3 blk(32, 4, 1);
+  const size_t smem = sizeof(float2) * kAsmSlots * kAsmThreads;
+  if (dfloat) {
+    const cudaError_t e = cudaFuncSetAttribute(k_assemble_stencil_df,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   for (int cls = 0; cls < 8; ++cls) {
     dim3 grd = elem_grid(nx, ny, nz, cls, blk);
     if (grd.x == 0 || grd.y == 0 || grd.z == 0) continue;
     const double d0 = 1.0 / (a[0] * a[0]), d1 = 1.0 / (a[1] * a[1]), d2 = 1.0 / (a[2] * a[2]);
     if (dfloat)
-      k_assemble_stencil<dflt><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, d0, d1, d2, C, flag, cls);
+      k_assemble_stencil_df<<<grd, blk, smem, st>>>(g, nx, ny, nz, xyz2, split_bits(d0), split_bits(d1),
+                                                    split_bits(d2), C, flag, cls);
     else
       k_assemble_stencil<double><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, d0, d1, d2, C, flag, cls);
     count_launches(1);
@@ -994,7 +1268,13 @@ cudaError_t launch_assemble_rhs(const Grid& g, int nx, int ny, int nz, const dou
       k_assemble_rhs<double, Q><<<grd, blk, 0, st>>>(g, nx, ny, nz, X, Y, Z, xyz2, u0, u2, f, cls); \
   } while (0)
     switch (quad & 3) {
-      case 0: MCW_RHS(0); break;
+      case 0:
+        if (dfloat)
+          k_assemble_rhs_df<<<grd, blk, sizeof(float2) * kRhsSlots * kAsmThreads, st>>>(
+              g, nx, ny, nz, xyz2, u2, f, cls);
+        else
+          MCW_RHS(0);
+        break;
       case 1: MCW_RHS(1); break;
       case 2: MCW_RHS(2); break;
       default: MCW_RHS(3); break;
@@ -1067,8 +1347,10 @@ cudaError_t launch_recover_center_df(int nx, int ny, int nz, const float2* xyz2,
                                      double* u, cudaStream_t st) {
   dim3 blk(32, 4, 1);
   dim3 grd((nx + 31) / 32, (ny + 3) / 4, nz);
-  k_recover_center_df<<<grd, blk, 0, st>>>(nx, ny, nz, xyz2, u2, u0c, lam2, 1.0 / (a[0] * a[0]),
-                                           1.0 / (a[1] * a[1]), 1.0 / (a[2] * a[2]), u);
+  k_recover_center_df<<<grd, blk, 0, st>>>(nx, ny, nz, xyz2, u2, u0c, lam2,
+                                           split_bits(1.0 / (a[0] * a[0])),
+                                           split_bits(1.0 / (a[1] * a[1])),
+                                           split_bits(1.0 / (a[2] * a[2])), u);
   count_launches(1);
   return cudaGetLastError();
 }
