@@ -438,23 +438,27 @@ def main():
     stream = torch.cuda.current_stream()
 
     copy_stream = torch.cuda.Stream(device=dev)
-    ev_u0n = torch.cuda.Event()
-    ev_uc = torch.cuda.Event()
+    ev_u0, ev_u0n, ev_uc = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
 
     def step(inputs=None, outputs=None, ev=None):
-        # With host buffers, the next time step's wind is copied in on a copy
-        # stream while the grid is assembled and the first wind solved, and
-        # the first wind field is copied out while the second is solved.
+        # With host buffers, the winds are copied in on a copy stream while
+        # the grid is assembled (the first) and the first wind is solved (the
+        # second), and the first wind field is copied out while the second
+        # is solved.
         if inputs is not None:
-            for dst, src in zip((X, Y, Z, U0), inputs[:4]):
+            for dst, src in zip((X, Y, Z), inputs[:3]):
                 dst.copy_(src, non_blocking=True)
             copy_stream.wait_stream(stream)
             with torch.cuda.stream(copy_stream):
+                U0.copy_(inputs[3], non_blocking=True)
+                ev_u0.record(copy_stream)
                 U0N.copy_(inputs[4], non_blocking=True)
                 ev_u0n.record(copy_stream)
         if ev: ev[0].record()
         plan.assemble(X, Y, Z)
         if ev: ev[1].record()
+        if inputs is not None:
+            stream.wait_event(ev_u0)
         _, s1 = m.mcwind_solve(plan.handle, U0, lam, RTOL, 100, 0)
         if ev: ev[2].record()
         m.mcwind_recover(plan.handle, U0, lam, u_c)

@@ -34,12 +34,14 @@ __global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, 
   int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= (int64_t)n * n) return;
   const int r = (int)(q / n), c = (int)(q % n);
-  const double piv = A[(int64_t)p * n + p];
+  // one division per thread (a float64 division is a long instruction
+  // sequence on the double pipe); the others multiply by the reciprocal
+  const double ip = 1.0 / A[(int64_t)p * n + p];
   double v;
-  if (r == p && c == p) v = 1.0 / piv;
-  else if (r == p) v = A[(int64_t)p * n + c] / piv;
-  else if (c == p) v = -A[(int64_t)r * n + p] / piv;
-  else v = A[q] - A[(int64_t)r * n + p] * (A[(int64_t)p * n + c] / piv);
+  if (r == p && c == p) v = ip;
+  else if (r == p) v = A[(int64_t)p * n + c] * ip;
+  else if (c == p) v = -A[(int64_t)r * n + p] * ip;
+  else v = A[q] - A[(int64_t)r * n + p] * (A[(int64_t)p * n + c] * ip);
   B[q] = v;
 }
 

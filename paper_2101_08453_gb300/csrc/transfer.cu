@@ -23,9 +23,11 @@ __device__ __forceinline__ void block_partial(double s, double* partials) {
 }
 
 // r = f - K x over one column, all k, both parities (blockIdx.z = parity).
-// MODE 0: write r (type T).  MODE 1 (T = double): write (float) r into r32
-// and zero e32, the start of one float32 correction cycle.  MODE 2: r = K x
-// (f unused) and the partials of x . K x instead of r . r.
+// MODE 0: write r (type T) and the partials of r . r.  MODE 3: write r only
+// (the residual of a cycle, before restriction: no norm, no double
+// arithmetic).  MODE 1 (T = double): write (float) r into r32 and zero e32,
+// the start of one float32 correction cycle.  MODE 2: r = K x (f unused) and
+// the partials of x . K x instead of r . r.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __restrict__ C,
                                                           const T* __restrict__ f,
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __res
           acc = f[b];
 #pragma unroll
           for (int s = 0; s < 27; ++s) acc -= coef(C, tot, b, s) * w[s / 9][s % 9];
-          ss += (double)acc * (double)acc;
+          if (MODE != 3) ss += (double)acc * (double)acc;
         }
         if (MODE != 1) r[b] = acc;
         else { r32[b] = (float)acc; e32[b] = 0.0f; }
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __res
       else { r32[b] = 0.0f; e32[b] = 0.0f; }
     }
   }
-  if (partials) block_partial(ss, partials);
+  if (MODE != 3 && partials) block_partial(ss, partials);
 }
 
 __device__ __forceinline__ bool node_of_thread(const Grid& g, int& i, int& j, int& k) {
@@ -275,7 +277,11 @@ cudaError_t launch_residual(const Grid& g, const T* C, const T* f, const T* x, T
                             double* partials, int cap, int* nblocks, cudaStream_t st) {
   dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
   if (partials && (int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
-  k_residual<T, 0><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, partials); count_launches(1);
+  if (partials)
+    k_residual<T, 0><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, partials);
+  else
+    k_residual<T, 3><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, nullptr);
+  count_launches(1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
   return cudaGetLastError();
 }
