@@ -4,6 +4,8 @@
 #include <map>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.cuh"
 
 using namespace mcw;
@@ -50,7 +52,18 @@ cudaError_t rhs_into(mcwind_plan p, const double* u0, double* f, cudaStream_t st
   return e;
 }
 
-// Records a CUDA event pair around a kernel class while profiling is on.
+// NVTX range names of the kernel classes (the order of the MCWIND_K_* kinds)
+const char* const kKindRange[MCWIND_K_KINDS] = {
+    "mcwind:assemble",      "mcwind:rap",           "mcwind:setup",
+    "mcwind:rhs",           "mcwind:outer_residual", "mcwind:smooth_fine",
+    "mcwind:smooth_coarse", "mcwind:residual_fine",  "mcwind:residual_coarse",
+    "mcwind:restrict",      "mcwind:prolong",        "mcwind:coarse_solve",
+    "mcwind:update",        "mcwind:recover",        "mcwind:krylov",
+    "mcwind:other"};
+
+// Around a kernel class: an NVTX range on the host thread (always; a
+// profiler can select launches by it, e.g. ncu --nvtx-include
+// "mcwind:smooth_fine/"), and, while profiling is on, a CUDA event pair.
 // A scope reserves its two events when it opens; finished pairs are folded
 // into the per-class totals whenever the stream is idle, and the event pool
 // is recycled only when no scope is open.
@@ -62,6 +75,7 @@ struct ProfScope {
   size_t idx = 0;
   bool on = false;
   ProfScope(mcwind_plan p_, int kind_, cudaStream_t st_) : p(p_), kind(kind_), st(st_) {
+    nvtxRangePushA(kKindRange[kind]);
     if (!p->prof) return;
     while (p->ev_used + 2 > p->ev_pool.size()) {
       cudaEvent_t e;
@@ -76,6 +90,7 @@ struct ProfScope {
     n0 = launches_now();
   }
   ~ProfScope() {
+    nvtxRangePop();
     if (!on) return;
     cudaEventRecord(p->ev_pool[idx + 1], st);
     p->prof_open -= 1;
