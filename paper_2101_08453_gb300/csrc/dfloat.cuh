@@ -44,10 +44,10 @@ static __host__ __device__ __noinline__ double pair_sum_by_conversion(float hi, 
 }
 static __host__ __device__ __noinline__ float float_by_conversion(double x) { return (float)x; }
 
-// (float)r for |r| < 2^29, rounded to nearest even, on the float pipe (the
-// int-to-float conversion instruction shares the double pipe's issue rate
-// on GB300): the two halves h = r >> 14 and l = r & 0x3FFF are read exactly
-// off the 1.5 * 2^23 bias, and h * 2^14 + l is rounded once by the FMA.
+// (float)r for |r| < 2^29, rounded to nearest even, on the float pipe (on
+// GB300 ncu counts the int-to-float conversion instruction as double-pipe
+// work): the two halves h = r >> 14 and l = r & 0x3FFF are read exactly off
+// the 1.5 * 2^23 bias, and h * 2^14 + l is rounded once by the FMA.
 __host__ __device__ inline float float_of_i29(int r) {
   const int h = r >> 14, l = r & 0x3FFF;
 #ifdef __CUDA_ARCH__
@@ -123,8 +123,8 @@ __device__ __forceinline__ double to_double(dflt a) { return (double)a.hi + (dou
 // (|k| <= 2^28), added to the magnitude's bit pattern.  That addition never
 // carries into the exponent; it borrows from it only when hi is a power of
 // two and lo lowers the magnitude, and then k is taken in the units of the
-// binade below.  Zeros give the sum's zero; hi outside [2^-74, 2^128), infinities
-// and NaN take the double-pipe path.
+// binade below.  Zeros give the sum's zero; hi outside [2^-74, 2^128),
+// infinities and NaN take the double-pipe path.
 __host__ __device__ inline double pair_to_double(float hi, float lo) {
 #ifdef __CUDA_ARCH__
   const unsigned uh = __float_as_uint(hi);

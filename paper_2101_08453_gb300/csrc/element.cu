@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(128, 4) k_assemble_stencil(Grid g, int nx, int
 
 // The float-pair stiffness kernel with its repeated work in loops.  Fully
 // unrolled, the per-element code is about 16 k instructions executed once
-// each, and fetching them bounds the kernel (ncu: most stalls wait for an
-// instruction).  Here the Gauss points, the 6 sign sums, the 15 transforms
+// each, and fetching them bounds the kernel (ncu: about half of the stall
+// cycles waited for an instruction).  Here the Gauss points, the 6 sign sums, the 15 transforms
 // of the 8 x 8 modal matrix and the 8 scatter rows are loops, and the values
 // they index by the loop counter live in shared memory (64 float pairs per
 // thread, each thread touching only its own column: no barrier).
