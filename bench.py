@@ -610,7 +610,9 @@ def main():
     def algo_units(cs, mixed):
         """Algorithmic units of one launch (node classes) or one call (element classes:
         3 + 8 or 1 + 8 launches, the input splits into float pairs and the 8
-        element-parity launches) of each class, per bound (derivations in the design doc)."""
+        element-parity launches) of each class, per bound: bytes moved for the
+        HBM-bound stencils, FMAs for the FP64-pipe-bound ones, float-pair
+        operations for the element kernels."""
         f64 = cs == 8
         return {
             # bytes: 26 off-diagonal coefficients + 1/diagonal + f + x read + x write per
