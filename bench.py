@@ -48,8 +48,8 @@ FP32_OPS_LOAD = 8308.0
 # FP32 pipe: 128 lanes per SM x 152 SMs x 2.07 GHz maximum SM clock
 FP32_PIPE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per unit of a launch, from one ncu capture of the
-# 600x600x15 case (profiles/k_gs_float_600x600x15.md), scaled by the units of
-# the full launch: FP32 smoother, bytes per node of the column group.
+# 600x600x15 case, scaled by the units of the full launch: FP32 smoother,
+# bytes per node of the column group.
 TRAFFIC_PER_UNIT = {"smooth_fine": (142.3, "ncu dram__bytes_read+write at 600x600x15, "
                                            "scaled by the column-group nodes")}
 

@@ -162,6 +162,11 @@ void mcwind_default_options(mcwind_options* opt);
 int mcwind_plan_create(int nx, int ny, int nz, const double a[3], double h1, const double* h3,
                        const mcwind_options* opt, mcwind_plan* out, size_t* workspace_bytes);
 
+/* The plan's options as they stand (host output; mcwind_plan_set_tuning
+ * changes nu_pre and nu_post) and its device workspace bytes.  Either output
+ * may be NULL.  Host only.  EINVAL on a NULL plan. */
+int mcwind_plan_query(mcwind_plan plan, mcwind_options* opt, size_t* workspace_bytes);
+
 /* Number of grid levels (finest = 0); negative code on a NULL plan. */
 int mcwind_plan_num_levels(mcwind_plan plan);
 
@@ -271,11 +276,12 @@ int mcwind_coarse_solve(mcwind_plan plan, const double* f, double* x, void* stre
  * recursive coarse correction, prolongation and post-smoothing of Sec. 3. */
 int mcwind_vcycle(mcwind_plan plan, int precision, double* x, const double* f, void* stream);
 
-/* Residual norms without allocating anything, for callers that cannot call
- * cudaMalloc when they check a solution (code running during CUDA graph
- * capture, where allocation is not capturable; host models whose own pool
- * owns all device memory).  The paper has no counterpart: this is the
- * solver's float64 convergence check (Sec. 3 is silent on it) exposed on its
+/* Residual norms without allocating anything.  For callers that cannot
+ * call cudaMalloc at the point where they check a solution: a host model that
+ * hands all device memory to its own pool at start-up and forbids later
+ * allocations, or a latency-bound loop in which an allocation (which may
+ * synchronize the whole device) is not allowed.  The paper has no
+ * counterpart: this is the solver's float64 convergence check exposed on its
  * own.  norms (device, 2 doubles) receives ||f_F||_2 and
  * ||f_F - K_FF lambda_F||_2 with K_FF the plan's assembled finest operator;
  * f and lambda are device [nz+1][ny+1][nx+1] (entries at fixed nodes are

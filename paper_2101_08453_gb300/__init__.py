@@ -81,6 +81,7 @@ def lib():
         "mcwind_plan_create": (_i, [_i, _i, _i, ctypes.POINTER(_d), _d, ctypes.POINTER(_d),
                                     ctypes.POINTER(Options), ctypes.POINTER(_vp),
                                     ctypes.POINTER(ctypes.c_size_t)]),
+        "mcwind_plan_query": (_i, [_vp, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_size_t)]),
         "mcwind_plan_num_levels": (_i, [_vp]),
         "mcwind_plan_level": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                                    ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -143,6 +144,53 @@ def _dev(t, name):
     return _vp(t.data_ptr())
 
 
+def _need(**tensors):
+    """Raise ValueError unless each tensor holds the number of values the
+    call reads or writes: name=(tensor, n) needs exactly n, name=(tensor, n,
+    "min") at least n.  Runs before anything is handed to the library, so a
+    short buffer never reaches a kernel."""
+    for name, spec in tensors.items():
+        t, n = spec[0], int(spec[1])
+        k = int(t.numel()) if hasattr(t, "numel") else -1
+        if (k < n) if len(spec) > 2 else (k != n):
+            want = f"at least {n}" if len(spec) > 2 else str(n)
+            raise ValueError(f"{name} holds {k} values; the plan needs {want}")
+
+
+def _dims(plan, level=0):
+    """Node counts (Nx, Ny, Nz) of a level of the plan."""
+    d = (_i * 3)()
+    _check(lib().mcwind_plan_level(plan, int(level), d, None, None, None), "mcwind_plan_level")
+    return d[0], d[1], d[2]
+
+
+def _nodes(plan, level=0):
+    Nx, Ny, Nz = _dims(plan, level)
+    return Nx * Ny * Nz
+
+
+def _cells(plan):
+    Nx, Ny, Nz = _dims(plan, 0)
+    return (Nx - 1) * (Ny - 1) * (Nz - 1)
+
+
+def plan_options(plan):
+    """The plan's options as they stand (mcwind_plan_query)."""
+    o = Options()
+    _check(lib().mcwind_plan_query(plan, ctypes.byref(o), None), "mcwind_plan_query")
+    return o
+
+
+def plan_workspace_bytes(plan):
+    n = ctypes.c_size_t()
+    _check(lib().mcwind_plan_query(plan, None, ctypes.byref(n)), "mcwind_plan_query")
+    return n.value
+
+
+def _u0_count(plan):
+    return 3 * (_cells(plan) if plan_options(plan).u0_at == U0_CENTERS else _nodes(plan))
+
+
 def default_options(**kw) -> Options:
     o = Options()
     lib().mcwind_default_options(ctypes.byref(o))
@@ -192,11 +240,16 @@ def mcwind_plan_destroy(plan):
 
 
 def mcwind_assemble(plan, workspace, X, Y, Z, stream=None):
+    n = _nodes(plan)
+    _need(X=(X, n), Y=(Y, n), Z=(Z, n))
+    if int(workspace.numel()) * workspace.element_size() < plan_workspace_bytes(plan):
+        raise ValueError("workspace is smaller than mcwind_plan_create reported")
     return _check(lib().mcwind_assemble(plan, _vp(workspace.data_ptr()), _dev(X, "X"), _dev(Y, "Y"),
                                         _dev(Z, "Z"), _stream(stream)), "mcwind_assemble")
 
 
 def mcwind_solve(plan, u0, lam, rtol=1e-8, max_cycles=100, flags=0, stream=None, raise_notconv=False):
+    _need(u0=(u0, _u0_count(plan)), lam=(lam, _nodes(plan)))
     st = Stats()
     ok = (MCWIND_OK,) if raise_notconv else (MCWIND_OK, MCWIND_ENOTCONV)
     rc = _check(lib().mcwind_solve(plan, _dev(u0, "u0"), _dev(lam, "lambda"), float(rtol),
@@ -206,6 +259,8 @@ def mcwind_solve(plan, u0, lam, rtol=1e-8, max_cycles=100, flags=0, stream=None,
 
 
 def mcwind_solve_rhs(plan, f, x, rtol=1e-8, max_cycles=100, flags=0, stream=None):
+    n = _nodes(plan)
+    _need(f=(f, n), x=(x, n))
     st = Stats()
     rc = _check(lib().mcwind_solve_rhs(plan, _dev(f, "f"), _dev(x, "x"), float(rtol), int(max_cycles),
                                        int(flags), ctypes.byref(st), _stream(stream)),
@@ -214,12 +269,16 @@ def mcwind_solve_rhs(plan, f, x, rtol=1e-8, max_cycles=100, flags=0, stream=None
 
 
 def mcwind_recover_adjoint(plan, gu, h, du0, stream=None):
+    n = _nodes(plan)
+    _need(gu=(gu, 3 * _cells(plan)), h=(h, n), du0=(du0, 3 * n))
     return _check(lib().mcwind_recover_adjoint(plan, _dev(gu, "gu"), _dev(h, "h"), _dev(du0, "du0"),
                                                _stream(stream)), "mcwind_recover_adjoint")
 
 
 def mcwind_adjoint_finish(plan, mu, lam, gu, du0, stream=None):
     """Returns dl/dlog a as a list of 3 floats (du0 updated in place)."""
+    n = _nodes(plan)
+    _need(mu=(mu, n), lam=(lam, n), gu=(gu, 3 * _cells(plan)), du0=(du0, 3 * n))
     out = (_d * 3)()
     _check(lib().mcwind_adjoint_finish(plan, _dev(mu, "mu"), _dev(lam, "lambda"), _dev(gu, "gu"),
                                        _dev(du0, "du0"), out, _stream(stream)), "mcwind_adjoint_finish")
@@ -227,51 +286,66 @@ def mcwind_adjoint_finish(plan, mu, lam, gu, du0, stream=None):
 
 
 def mcwind_recover(plan, u0, lam, u, where=AT_CENTERS, stream=None):
+    _need(u0=(u0, _u0_count(plan)), lam=(lam, _nodes(plan)),
+          u=(u, (3 if where == AT_CENTERS else 24) * _cells(plan)))
     return _check(lib().mcwind_recover(plan, _dev(u0, "u0"), _dev(lam, "lambda"), _dev(u, "u"),
                                        int(where), _stream(stream)), "mcwind_recover")
 
 
 def mcwind_rhs(plan, u0, f, stream=None):
+    _need(u0=(u0, _u0_count(plan)), f=(f, _nodes(plan)))
     return _check(lib().mcwind_rhs(plan, _dev(u0, "u0"), _dev(f, "f"), _stream(stream)), "mcwind_rhs")
 
 
 def mcwind_weak_div(plan, ug, out, stream=None):
+    _need(ug=(ug, 24 * _cells(plan)), out=(out, _nodes(plan)))
     return _check(lib().mcwind_weak_div(plan, _dev(ug, "ug"), _dev(out, "out"), _stream(stream)),
                   "mcwind_weak_div")
 
 
 def mcwind_level_stencil(plan, level, precision, out, stream=None):
+    _need(out=(out, 27 * _nodes(plan, level)))
     return _check(lib().mcwind_level_stencil(plan, level, precision, _dev(out, "out"), _stream(stream)),
                   "mcwind_level_stencil")
 
 
 def mcwind_level_residual(plan, level, precision, x, f, r, stream=None):
+    n = _nodes(plan, level)
+    _need(x=(x, n), f=(f, n), r=(r, n))
     return _check(lib().mcwind_level_residual(plan, level, precision, _dev(x, "x"), _dev(f, "f"),
                                               _dev(r, "r"), _stream(stream)), "mcwind_level_residual")
 
 
 def mcwind_level_smooth(plan, level, precision, x, f, sweeps, direction, stream=None):
+    n = _nodes(plan, level)
+    _need(x=(x, n), f=(f, n))
     return _check(lib().mcwind_level_smooth(plan, level, precision, _dev(x, "x"), _dev(f, "f"),
                                             int(sweeps), int(direction), _stream(stream)),
                   "mcwind_level_smooth")
 
 
 def mcwind_level_restrict(plan, level, precision, r, fc, stream=None):
+    _need(r=(r, _nodes(plan, level)), fc=(fc, _nodes(plan, level + 1)))
     return _check(lib().mcwind_level_restrict(plan, level, precision, _dev(r, "r"), _dev(fc, "fc"),
                                               _stream(stream)), "mcwind_level_restrict")
 
 
 def mcwind_level_prolong(plan, level, precision, ec, x, stream=None):
+    _need(ec=(ec, _nodes(plan, level + 1)), x=(x, _nodes(plan, level)))
     return _check(lib().mcwind_level_prolong(plan, level, precision, _dev(ec, "ec"), _dev(x, "x"),
                                              _stream(stream)), "mcwind_level_prolong")
 
 
 def mcwind_coarse_solve(plan, f, x, stream=None):
+    n = _nodes(plan, mcwind_plan_num_levels(plan) - 1)
+    _need(f=(f, n), x=(x, n))
     return _check(lib().mcwind_coarse_solve(plan, _dev(f, "f"), _dev(x, "x"), _stream(stream)),
                   "mcwind_coarse_solve")
 
 
 def mcwind_vcycle(plan, precision, x, f, stream=None):
+    n = _nodes(plan)
+    _need(x=(x, n), f=(f, n))
     return _check(lib().mcwind_vcycle(plan, precision, _dev(x, "x"), _dev(f, "f"), _stream(stream)),
                   "mcwind_vcycle")
 
@@ -279,10 +353,13 @@ def mcwind_vcycle(plan, precision, x, f, stream=None):
 def mcwind_residual_norm_noalloc(plan, f, lam, norms, stream=None):
     """(||f_F||, ||f_F - K_FF lambda_F||) into the device tensor norms[2],
     allocating nothing: for callers that cannot call cudaMalloc when they
-    check a solution (during CUDA graph capture, or under a host model that
-    owns all device memory).  Its scratch is a static device array inside
-    the library, shared by all calls: calls that overlap on the GPU race.
-    The first call on a device must come before any stream capture."""
+    check a solution (a host model whose own pool owns all device memory, or
+    a loop in which an allocation, which may synchronize the device, is not
+    allowed).  Its scratch is a static device array inside the library,
+    shared by all calls: calls that overlap on the GPU race.  The first call
+    on a device must come before any stream capture."""
+    n = _nodes(plan)
+    _need(f=(f, n), lam=(lam, n), norms=(norms, 2, "min"))
     return _check(lib().mcwind_residual_norm_noalloc(plan, _dev(f, "f"), _dev(lam, "lambda"),
                                                      _dev(norms, "norms"), _stream(stream)),
                   "mcwind_residual_norm_noalloc")
@@ -320,6 +397,10 @@ class Batch:
         n = len(self.plans)
         if lams is None:
             lams = [torch.zeros(p.node_shape, dtype=torch.float64, device="cuda") for p in self.plans]
+        if len(u0s) != n or len(lams) != n:
+            raise ValueError(f"a batch of {n} domains needs {n} winds and {n} lambdas")
+        for p, u, l in zip(self.plans, u0s, lams):
+            _need(u0=(u, _u0_count(p.handle)), lam=(l, _nodes(p.handle)))
         u_arr = (_vp * n)(*[_dev(u, "u0").value for u in u0s])
         l_arr = (_vp * n)(*[_dev(l, "lambda").value for l in lams])
         stats = (Stats * n)()

@@ -1,13 +1,13 @@
 // Residual norms that allocate nothing: mcwind_residual_norm_noalloc.
 //
 // Why it exists: some callers cannot call cudaMalloc at the point where they
-// want to check a solution -- for example code that runs while a CUDA graph
-// is being captured (allocation is not a capturable operation), or a host
-// model that hands all device memory to its own pool at start-up and forbids
-// later allocations.  This entry point computes the same two norms as the
-// solver's convergence check without asking for any memory: its per-block
-// partial sums live in the file-scope array below, which every GPU that
-// loads the library holds until the process exits.
+// want to check a solution -- for example a host model that hands all device
+// memory to its own pool at start-up and forbids later allocations, or a
+// latency-bound loop in which an allocation (which may synchronize the whole
+// device) is not allowed.  This entry point computes the same two norms as
+// the solver's convergence check without asking for any memory: its
+// per-block partial sums live in the file-scope array below, which every GPU
+// that loads the library holds until the process exits.
 //
 // The array is shared by every call, on every stream, and keeps the last
 // call's contents; nothing in it has to start at zero (each call writes every

@@ -221,6 +221,13 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   return MCWIND_OK;
 }
 
+extern "C" int mcwind_plan_query(mcwind_plan p, mcwind_options* opt, size_t* workspace_bytes) {
+  if (!p) return MCWIND_EINVAL;
+  if (opt) *opt = p->opt;
+  if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+  return MCWIND_OK;
+}
+
 extern "C" int mcwind_plan_num_levels(mcwind_plan p) {
   return p ? (int)p->lv.size() : MCWIND_EINVAL;
 }

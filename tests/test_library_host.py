@@ -109,6 +109,24 @@ def test_planner_matches_oracle(name, maker, a, rule, cmax):
                 assert got[key] == want[key], (l, key, got, want)
 
 
+@pytest.mark.parametrize("rule,key", [(0, "levels_paper"), (1, "levels_operator")])
+def test_planner_matches_hand_derived_aniso64(rule, key):
+    """The library's planner against the hand-derived hierarchies of the
+    semicoarsening rule of Sec. 3 (a = (0.5, 1, 10), both ratio readings)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "plan_aniso64.json")))
+    c = g["case"]
+    h3 = [c["h3_first"] * c["h3_growth"] ** k for k in range(c["nz"])]
+    plan = m.Plan(c["nx"], c["ny"], c["nz"], c["a"], c["h1"], h3, coarsen_rule=rule,
+                  coarsest_max=c["coarsest_max"])
+    assert plan.num_levels == len(g[key])
+    for l, want in enumerate(g[key]):
+        got = plan.level(l)
+        for name, value in want.items():
+            assert got[name] == value, (l, name, got, want)
+
+
 def test_cg_workspace_is_larger():
     h3 = [5.0, 6.0, 7.0, 8.0]
     _, ws0 = m.mcwind_plan_create(64, 48, 4, (1, 1, 1), 30.0, h3)

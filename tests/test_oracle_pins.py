@@ -263,6 +263,44 @@ def test_plan_hill64_matches_hand_derivation():
             assert got[key] == want[key], (key, got, want)
 
 
+def _aniso64_levels(rule, a=None):
+    g = json.load(open(os.path.join(GOLD, "plan_aniso64.json")))
+    c = g["case"]
+    h3 = [c["h3_first"] * c["h3_growth"] ** k for k in range(c["nz"])]
+    a = c["a"] if a is None else a
+    return g, oracle.plan_levels(c["nx"], c["ny"], c["nz"], c["h1"], h3, a, rule,
+                                 c["coarsest_max"])
+
+
+def _same_levels(got, want):
+    return len(got) == len(want) and all(
+        all(gl.get(key) == wl[key] for key in wl) for gl, wl in zip(got, want))
+
+
+@pytest.mark.parametrize("rule", ["paper", "operator"])
+def test_plan_aniso64_matches_hand_derivation(rule):
+    """Both readings of the semicoarsening ratio of Sec. 3 against a
+    hierarchy derived by hand where they disagree (a1 != 1, a3 = 10): the
+    operator reading merges layers one by one above the ground."""
+    g, lv = _aniso64_levels(rule)
+    assert _same_levels(lv, g["levels_" + rule]), (lv, g["levels_" + rule])
+
+
+@pytest.mark.parametrize("rule,mutated", [
+    ("paper", (0.5, 1.0, 1.0)),        # a3 dropped
+    ("paper", (10.0, 1.0, 0.5)),       # a1 and a3 swapped
+    ("operator", (1.0, 1.0, 10.0)),    # a1 dropped
+    ("operator", (0.5, 1.0, 1.0)),     # a3 dropped
+    ("operator", (10.0, 1.0, 0.5)),    # a1 and a3 swapped
+])
+def test_plan_aniso64_detects_penalty_slips(rule, mutated):
+    """The fixture fixes how a1 and a3 enter each ratio: planning with a
+    penalty vector that a dropped or swapped constant would produce gives a
+    different hierarchy, so such a slip in the planner cannot pass."""
+    g, lv = _aniso64_levels(rule, mutated)
+    assert not _same_levels(lv, g["levels_" + rule])
+
+
 def test_p10_galerkin_nested_uniform_grid():
     """On a uniform box grid with full 2x coarsening the coarse space is the
     Q1 space of the 2h grid, so P^T K P is the 2h stiffness (Sec. 3)."""
