@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mcwind", choices=["mcwind", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--op-form", default="stored", choices=["stored", "separable"],
+                    help="float32 cycle on stored 27-point rows or on the column x layer "
+                         "factors of the shift-form grid (mixed precision)")
     ap.add_argument("--cells", type=int, nargs=3, default=list(CELLS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -430,8 +433,10 @@ def main():
     n_free = case.n_free
 
     X, Y, Z, U0, U0N = (torch.from_numpy(a).to(dev) for a in (case.X, case.Y, case.Z, case.u0, u0n_np))
-    plan = m.Plan.for_case(case, precision=prec)
+    op_form = m.OP_SEPARABLE if (args.op_form == "separable" and prec == m.PREC_MIXED) else m.OP_STORED
+    plan = m.Plan.for_case(case, precision=prec, op_form=op_form)
     plan_cpc = plan.options.cycles_per_check
+    plan_ws = plan.workspace_bytes
     lam = torch.zeros(plan.node_shape, dtype=torch.float64, device=dev)
     u_c = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)
     u_w = torch.empty_like(u_c)
@@ -568,7 +573,7 @@ def main():
         del plan
         torch.cuda.empty_cache()
         # the same solves accelerated by conjugate gradients (one V-cycle per iteration)
-        pcg = m.Plan.for_case(case, precision=m.PREC_MIXED, accel=m.ACCEL_CG)
+        pcg = m.Plan.for_case(case, precision=m.PREC_MIXED, accel=m.ACCEL_CG, op_form=op_form)
         pcg.assemble(X, Y, Z)
         lam.zero_()
         time_solve(pcg, U0, False)
@@ -686,6 +691,8 @@ def main():
                                f"u0 from a 100x100 coarse wind): assemble + hierarchy, cold solve + "
                                f"recover, 2%-perturbed warm solve + recover, to rtol {RTOL}",
                    "cells": [nx, ny, nz], "n_free": n_free, "precision": args.precision,
+                   "op_form": args.op_form if prec == m.PREC_MIXED else "stored",
+                   "workspace_gb": plan_ws / 1e9,
                    "rtol": RTOL, "levels": plan_levels if False else None,
                    "l2": "inputs larger than L2 (X, Y, Z, u0, u0' = %.1f GB resident)" % (
                        9 * n_nodes * 8 / 1e9),

@@ -61,7 +61,9 @@ enum {
   MCWIND_ENOTCONV = -4,   /* max_cycles reached above rtol; lambda and stats are written */
   MCWIND_ECUDA = -5,      /* a CUDA call failed */
   MCWIND_ESTATE = -6,     /* call out of order (e.g. solve before assemble) */
-  MCWIND_ETIMEOUT = -7    /* reserved for bounded device waits */
+  MCWIND_ETIMEOUT = -7,   /* a kernel's bounded device wait ran out (a copy that did not
+                             arrive within its limit); the solve stops, lambda unwritten */
+  MCWIND_ESHIFT = -8      /* MCWIND_OP_SEPARABLE on a grid that is not in shift form */
 };
 
 enum { MCWIND_PREC_F64 = 0, MCWIND_PREC_MIXED = 1 };
@@ -72,6 +74,7 @@ enum { MCWIND_FORWARD = 0, MCWIND_BACKWARD = 1 };
 enum { MCWIND_ACCEL_NONE = 0, MCWIND_ACCEL_CG = 1 };
 enum { MCWIND_U0_NODES = 0, MCWIND_U0_CENTERS = 1 };
 enum { MCWIND_ARITH_F64 = 0, MCWIND_ARITH_DFLOAT = 1 };
+enum { MCWIND_OP_STORED = 0, MCWIND_OP_SEPARABLE = 1 };
 
 #define MCWIND_WARM 1u        /* mcwind_solve flag: start from the caller's lambda */
 #define MCWIND_HIST 256
@@ -136,6 +139,22 @@ typedef struct {
      multiple of this (or max_cycles).  Ignored with MCWIND_ACCEL_CG (one
      cycle per iteration). */
   int cycles_per_check;
+  /* Form of the float32 cycle's operators (MCWIND_PREC_MIXED).
+     MCWIND_OP_STORED (default): the 27 coefficients of every node are stored
+     on every level, float64 and a float32 copy (general hexahedra).
+     MCWIND_OP_SEPARABLE: for a terrain-following grid in shift form (X and Y
+     the same in every layer, z = z_s(x, y) + zeta_k, Sec. 2) the stiffness of
+     Eq. 5 is exactly sum_t H_t (x) V_t, four horizontal 9-point operators on
+     the node columns times four vertical tridiagonal ones on the layers (the
+     element Jacobian splits into the terrain's slopes and the layer
+     thickness), and the Galerkin products of Eq. 7 keep that form.  The
+     float32 cycle then stores 36 values per column and 12 per layer on every
+     level and rebuilds each row as it smooths; float64 operators are kept
+     for the finest level (the float64 residual of the refinement) and the
+     coarsest (its direct solve) only.  Needs MCWIND_PREC_MIXED;
+     mcwind_assemble returns MCWIND_ESHIFT when the grid is not in shift form
+     (to 1e-10 of the coordinates' magnitude). */
+  int op_form;
 } mcwind_options;
 
 typedef struct {
@@ -193,7 +212,9 @@ int mcwind_assemble(mcwind_plan plan, void* workspace, const double* X, const do
  * entries are ignored), always written (0 at fixed nodes).  stats: host,
  * may be NULL.  Reads the residual norm back after every cycle (one stream
  * synchronization per cycle).  Returns OK, ENOTCONV (lambda and stats still
- * written), ENONFINITE (u0 not finite), ESTATE (not assembled). */
+ * written), ENONFINITE (u0 not finite), ESTATE (not assembled), ETIMEOUT (a
+ * kernel's bounded wait ran out; the status stays set until the plan is
+ * assembled again). */
 int mcwind_solve(mcwind_plan plan, const double* u0, double* lambda, double rtol, int max_cycles,
                  unsigned flags, mcwind_stats* stats, void* stream);
 
@@ -244,7 +265,11 @@ int mcwind_weak_div(mcwind_plan plan, const double* ug, double* out, void* strea
  * precision selects the float64 or the float32 kernels (float32 needs a
  * plan created with MCWIND_PREC_MIXED); float32 work converts at entry and
  * exit.  These calls use the level's internal buffers: they must not run
- * while mcwind_solve runs on the same plan. */
+ * while mcwind_solve runs on the same plan.  With MCWIND_OP_SEPARABLE the
+ * float32 calls use the separable operator; the float64 residual and
+ * smoother exist on the finest and the coarsest level only (EINVAL
+ * elsewhere), the float64 V-cycle not at all, and the stencil export
+ * rebuilds the rows from the float64 or float32 factors. */
 
 /* Export the level's stencil: out device [27][Nz][Ny][Nx], plane
  * s = (di+1) + 3(dj+1) + 9(dk+1) holding the coefficient of node
@@ -264,6 +289,12 @@ int mcwind_level_smooth(mcwind_plan plan, int level, int precision, double* x, c
 /* f_c = P^T r (Eq. 7 first row) from level to level+1. */
 int mcwind_level_restrict(mcwind_plan plan, int level, int precision, const double* r,
                           double* fc, void* stream);
+
+/* f_c = P^T (f - K x) (Eq. 7 first row) from level to level+1, the residual
+ * not stored where the float32 separable cycle fuses the two (a transfer
+ * that keeps the columns). */
+int mcwind_level_residual_restrict(mcwind_plan plan, int level, int precision, const double* x,
+                                   const double* f, double* fc, void* stream);
 
 /* x += P e_c (Eq. 7 last row) from level+1 to level. */
 int mcwind_level_prolong(mcwind_plan plan, int level, int precision, const double* ec, double* x,
@@ -339,8 +370,8 @@ int mcwind_plan_set_tuning(mcwind_plan plan, int nu_pre, int nu_post, int gs_blo
  * caller's stream around each launch of the class while profiling is on). */
 enum {
   MCWIND_K_ASSEMBLE = 0,    /* element stiffness, 2x2x2 Gauss, scatter */
-  MCWIND_K_RAP,             /* Galerkin stages K_c = P^T K P */
-  MCWIND_K_SETUP,           /* stencil finalize, float32 copy, coarsest inverse */
+  MCWIND_K_RAP,             /* Galerkin stages K_c = P^T K P (of the factors when separable) */
+  MCWIND_K_SETUP,           /* stencil finalize, float32 copy, coarsest inverse, factors */
   MCWIND_K_RHS,             /* load vector of Eq. 5 */
   MCWIND_K_OUTER_RESIDUAL,  /* float64 residual + norm on the finest level */
   MCWIND_K_SMOOTH_FINE,     /* Gauss-Seidel on the finest level */

@@ -23,6 +23,7 @@ MCWIND_ENOTCONV = -4
 MCWIND_ECUDA = -5
 MCWIND_ESTATE = -6
 MCWIND_ETIMEOUT = -7
+MCWIND_ESHIFT = -8
 PREC_F64, PREC_MIXED = 0, 1
 RHS_GAUSS8, RHS_CENTER1 = 0, 1
 RULE_PAPER, RULE_OPERATOR = 0, 1
@@ -31,6 +32,7 @@ FORWARD, BACKWARD = 0, 1
 ACCEL_NONE, ACCEL_CG = 0, 1
 U0_NODES, U0_CENTERS = 0, 1
 ARITH_F64, ARITH_DFLOAT = 0, 1
+OP_STORED, OP_SEPARABLE = 0, 1
 WARM = 1
 HIST = 256
 
@@ -50,7 +52,8 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("rhs_quad", ctypes.c_int),
                 ("post_reverse", ctypes.c_int), ("accel", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("u0_at", ctypes.c_int),
-                ("element_arith", ctypes.c_int), ("cycles_per_check", ctypes.c_int)]
+                ("element_arith", ctypes.c_int), ("cycles_per_check", ctypes.c_int),
+                ("op_form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +97,7 @@ def lib():
         "mcwind_level_residual": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
         "mcwind_level_smooth": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, _vp]),
         "mcwind_level_restrict": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+        "mcwind_level_residual_restrict": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
         "mcwind_level_prolong": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
         "mcwind_coarse_solve": (_i, [_vp, _vp, _vp, _vp]),
         "mcwind_vcycle": (_i, [_vp, _i, _vp, _vp, _vp]),
@@ -328,6 +332,15 @@ def mcwind_level_restrict(plan, level, precision, r, fc, stream=None):
     _need(r=(r, _nodes(plan, level)), fc=(fc, _nodes(plan, level + 1)))
     return _check(lib().mcwind_level_restrict(plan, level, precision, _dev(r, "r"), _dev(fc, "fc"),
                                               _stream(stream)), "mcwind_level_restrict")
+
+
+def mcwind_level_residual_restrict(plan, level, precision, x, f, fc, stream=None):
+    n = _nodes(plan, level)
+    _need(x=(x, n), f=(f, n), fc=(fc, _nodes(plan, level + 1)))
+    return _check(lib().mcwind_level_residual_restrict(plan, level, precision, _dev(x, "x"),
+                                                       _dev(f, "f"), _dev(fc, "fc"),
+                                                       _stream(stream)),
+                  "mcwind_level_residual_restrict")
 
 
 def mcwind_level_prolong(plan, level, precision, ec, x, stream=None):

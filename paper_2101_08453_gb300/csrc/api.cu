@@ -121,6 +121,8 @@ P* at(mcwind_plan p, P* offset) {
 
 double* scal(mcwind_plan p) { return (double*)(p->ws + p->off_scalars); }
 int* flagp(mcwind_plan p) { return (int*)(p->ws + p->off_scalars + 128); }
+// device status word: bits set by kernels whose bounded waits ran out
+int* statusp(mcwind_plan p) { return (int*)(p->ws + p->off_scalars + 132); }
 double* partials(mcwind_plan p) { return (double*)(p->ws + p->off_partials); }
 int* cfree(mcwind_plan p) { return (int*)(p->ws + p->off_cfree); }
 
@@ -151,6 +153,13 @@ struct Sel<float> {
   static Ptr32 get(mcwind_plan p, int l) { return lv32(p, l); }
 };
 
+// separable float32 factors of level l
+const float* sep_h32(mcwind_plan p, int l) { return at(p, p->lv[l].H32); }
+const float* sep_v32(mcwind_plan p, int l) { return at(p, p->lv[l].V32); }
+
+template <typename T>
+constexpr bool is_f32() { return sizeof(T) == 4; }
+
 double* dense_inv(mcwind_plan p) {
   // result of the Gauss-Jordan ping-pong: n even -> first buffer, odd -> second
   double* A = (double*)(p->ws + p->off_dense);
@@ -166,15 +175,52 @@ int smooth(mcwind_plan p, int l, int sweeps, int direction, cudaStream_t st,
   auto P = Sel<T>::get(p, l);
   const Grid& g = p->lv[l].g;
   PROF(l == 0 ? MCWIND_K_SMOOTH_FINE : MCWIND_K_SMOOTH_COARSE);
+  const bool sep = is_f32<T>() && p->sep;
   for (int s = 0; s < sweeps; ++s)
     for (int q = 0; q < 4; ++q) {
       const int grp = direction == MCWIND_FORWARD ? q : 3 - q;
-      if (s == 0 && q == 0 && zero_start && direction == MCWIND_FORWARD)
+      const int up = direction == MCWIND_FORWARD ? 1 : 0;
+      const bool first = s == 0 && q == 0 && zero_start && direction == MCWIND_FORWARD;
+      if (sep) {
+        const float* H = sep_h32(p, l);
+        const float* V = sep_v32(p, l);
+        if (first)
+          CK(launch_gs_sep_zero_start(g, H, V, (const float*)P.f, (float*)P.x, grp, st));
+        else
+          CK(launch_gs_sep_staged(g, H, V, (const float*)P.f, (float*)P.x, grp, up, statusp(p),
+                                  st));
+      } else if (first) {
         CK(launch_gs_zero_start<T>(g, P.C, P.f, P.x, grp, st));
-      else
-        CK(launch_gs_group<T>(g, P.C, P.f, P.x, grp, direction == MCWIND_FORWARD ? 1 : 0,
-                              p->gs_rows, st));
+      } else {
+        CK(launch_gs_group<T>(g, P.C, P.f, P.x, grp, up, p->gs_rows, st));
+      }
     }
+  return MCWIND_OK;
+}
+
+// f_c = P^T (f - K x) from level l to l+1 in the cycle's precision: the
+// separable float32 operator fuses the two when the transfer keeps the
+// columns (no residual stored), else r is formed and restricted.
+template <typename T>
+int residual_restrict(mcwind_plan p, int l, cudaStream_t st) {
+  Level& L = p->lv[l];
+  auto P = Sel<T>::get(p, l);
+  auto Q = Sel<T>::get(p, l + 1);
+  if (is_f32<T>() && p->sep) {
+    const bool fuse = !L.hx && !L.hy;
+    {
+      PROF(l == 0 ? MCWIND_K_RESIDUAL_FINE : MCWIND_K_RESIDUAL_COARSE);
+      CK(launch_residual_sep(L.g, fuse ? &L.tr : nullptr, sep_h32(p, l), sep_v32(p, l),
+                             (const float*)P.f, (const float*)P.x,
+                             fuse ? (float*)Q.f : (float*)P.r, st));
+    }
+    if (fuse) return MCWIND_OK;
+  } else {
+    PROF(l == 0 ? MCWIND_K_RESIDUAL_FINE : MCWIND_K_RESIDUAL_COARSE);
+    CK(launch_residual<T>(L.g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
+  }
+  PROF(MCWIND_K_RESTRICT);
+  CK(launch_restrict<T>(L.g, p->lv[l + 1].g, L.tr, P.r, Q.f, st));
   return MCWIND_OK;
 }
 
@@ -193,15 +239,8 @@ int vcycle(mcwind_plan p, int l, cudaStream_t st, bool x_zero = false) {
   const bool zs = (l > 0 || x_zero) && p->opt.nu_pre >= 1;
   if (l > 0 && !zs) CK(cudaMemsetAsync(P.x, 0, sizeof(T) * (size_t)L.g.total, st));
   CKR(smooth<T>(p, l, p->opt.nu_pre, MCWIND_FORWARD, st, zs));
-  {
-    PROF(l == 0 ? MCWIND_K_RESIDUAL_FINE : MCWIND_K_RESIDUAL_COARSE);
-    CK(launch_residual<T>(L.g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
-  }
+  CKR(residual_restrict<T>(p, l, st));
   auto Q = Sel<T>::get(p, l + 1);
-  {
-    PROF(MCWIND_K_RESTRICT);
-    CK(launch_restrict<T>(L.g, p->lv[l + 1].g, L.tr, P.r, Q.f, st));
-  }
   CKR(vcycle<T>(p, l + 1, st, true));
   {
     PROF(MCWIND_K_PROLONG);
@@ -211,12 +250,15 @@ int vcycle(mcwind_plan p, int l, cudaStream_t st, bool x_zero = false) {
   return MCWIND_OK;
 }
 
-int check_level(mcwind_plan p, int level, int precision) {
+// op64: the call applies the level's float64 operator (absent on the
+// intermediate levels of the separable form)
+int check_level(mcwind_plan p, int level, int precision, bool op64 = false) {
   if (!p) return MCWIND_EINVAL;
   if (!p->assembled) return MCWIND_ESTATE;
   if (level < 0 || level >= (int)p->lv.size()) return MCWIND_EINVAL;
   if (precision != MCWIND_PREC_F64 && precision != MCWIND_PREC_MIXED) return MCWIND_EINVAL;
   if (precision == MCWIND_PREC_MIXED && p->opt.precision != MCWIND_PREC_MIXED) return MCWIND_EINVAL;
+  if (op64 && precision == MCWIND_PREC_F64 && !p->lv[level].has_c64) return MCWIND_EINVAL;
   return MCWIND_OK;
 }
 
@@ -308,11 +350,14 @@ int run_iteration(mcwind_plan p, cudaStream_t st, Body body) {
   return MCWIND_OK;
 }
 
-// copy device scalars [first, first + n) to host (synchronizes the stream)
+// copy device scalars [first, first + n) to host (synchronizes the stream);
+// ETIMEOUT when a kernel's bounded wait has run out since the last assembly
 int read_scalars(mcwind_plan p, double* host, int first, int n, cudaStream_t st) {
   CK(cudaMemcpyAsync(host, scal(p) + first, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&p->status_host, statusp(p), sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (p->prof) prof_fold(p);
+  if (p->status_host != 0) return MCWIND_ETIMEOUT;
   return MCWIND_OK;
 }
 
@@ -330,6 +375,7 @@ extern "C" const char* mcwind_strerror(int code) {
     case MCWIND_ECUDA: return "CUDA error";
     case MCWIND_ESTATE: return "plan not assembled";
     case MCWIND_ETIMEOUT: return "device wait timed out";
+    case MCWIND_ESHIFT: return "grid not terrain-following in shift form (separable operator)";
     default: return "unknown error";
   }
 }
@@ -341,6 +387,11 @@ extern "C" void mcwind_plan_destroy(mcwind_plan p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
 }
+
+namespace {
+int assemble_hierarchy(mcwind_plan p, cudaStream_t st);
+int assemble_separable(mcwind_plan p, cudaStream_t st);
+}  // namespace
 
 extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, const double* Y,
                                const double* Z, void* stream) {
@@ -380,6 +431,37 @@ extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, 
     PROF(MCWIND_K_SETUP);
     CK(launch_stencil_finalize(L0.g, at(p, L0.C64), flagp(p), st));
   }
+  if (p->sep) {
+    CKR(assemble_separable(p, st));
+  } else {
+    CKR(assemble_hierarchy(p, st));
+  }
+  // coarsest direct solver
+  Level& Lc = p->lv.back();
+  double* A = (double*)(p->ws + p->off_dense);
+  double* B = A + (size_t)p->n_coarse * p->n_coarse;
+  {
+    PROF(MCWIND_K_SETUP);
+    CK(launch_coarse_index(Lc.g, cfree(p), st));
+    CK(launch_dense_gather(Lc.g, at(p, Lc.C64), cfree(p), p->n_coarse, A, st));
+    double* res = nullptr;
+    CK(launch_dense_invert(A, B, p->n_coarse, &res, st));
+  }
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, flagp(p), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (p->prof) prof_fold(p);
+  if (flag & 8) return MCWIND_ESHIFT;
+  if (flag) return MCWIND_EGEOM;
+  p->assembled = true;
+  return MCWIND_OK;
+}
+
+namespace {
+
+// Galerkin operators of the stored form: K_c = P^T K P one direction at a
+// time on every level, finalized, and their float32 copies (mixed precision).
+int assemble_hierarchy(mcwind_plan p, cudaStream_t st) {
   double* tmpA = (double*)(p->ws + p->off_tmp);
   double* tmpB = (double*)(p->ws + p->off_tmp + p->tmp_bytes);
   for (size_t l = 0; l + 1 < p->lv.size(); ++l) {
@@ -407,22 +489,45 @@ extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, 
   if (p->opt.precision == MCWIND_PREC_MIXED)
     for (size_t l = 0; l < p->lv.size(); ++l)
       CK(launch_stencil_to_f32(p->lv[l].g, at(p, p->lv[l].C64), at(p, p->lv[l].C32), st));
-  // coarsest direct solver
-  Level& Lc = p->lv.back();
-  double* A = (double*)(p->ws + p->off_dense);
-  double* B = A + (size_t)p->n_coarse * p->n_coarse;
-  CK(launch_coarse_index(Lc.g, cfree(p), st));
-  CK(launch_dense_gather(Lc.g, at(p, Lc.C64), cfree(p), p->n_coarse, A, st));
-  double* res = nullptr;
-  CK(launch_dense_invert(A, B, p->n_coarse, &res, st));
-  int flag = 0;
-  CK(cudaMemcpyAsync(&flag, flagp(p), sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (p->prof) prof_fold(p);
-  if (flag) return MCWIND_EGEOM;
-  p->assembled = true;
   return MCWIND_OK;
 }
+
+// Separable form: check the shift form, build the finest factors from the
+// ground layer and the layer thicknesses, carry them down the hierarchy
+// (horizontal and vertical Galerkin products), and expand the coarsest
+// level's float64 rows for its direct solve.
+int assemble_separable(mcwind_plan p, cudaStream_t st) {
+  Level& L0 = p->lv[0];
+  const int Nx = p->nx + 1, Ny = p->ny + 1, Nz = p->nz + 1;
+  {
+    PROF(MCWIND_K_SETUP);
+    CK(launch_shift_check(Nx, Ny, Nz, p->X, p->Y, p->Z, flagp(p), st));
+    CK(launch_hfactors(L0.g, p->X, p->Y, p->Z, p->a, at(p, L0.H64), at(p, L0.H32), flagp(p), st));
+    CK(launch_vfactor0(Nx, Ny, Nz, p->Z, at(p, L0.V64), at(p, L0.V32), st));
+  }
+  double* tmp = (double*)(p->ws + p->off_tmp);
+  for (size_t l = 0; l + 1 < p->lv.size(); ++l) {
+    Level& F = p->lv[l];
+    Level& Cl = p->lv[l + 1];
+    PROF(MCWIND_K_RAP);
+    if (F.hx && F.hy) {
+      const Grid mid = make_grid(Cl.g.Nx, F.g.Ny, 1);
+      CK(launch_hgalerkin(0, F.g, mid, at(p, F.H64), tmp, st));
+      CK(launch_hgalerkin(1, mid, Cl.g, tmp, at(p, Cl.H64), st));
+    } else if (F.hx || F.hy) {
+      CK(launch_hgalerkin(F.hx ? 0 : 1, F.g, Cl.g, at(p, F.H64), at(p, Cl.H64), st));
+    }
+    if (!Cl.h_shared) CK(launch_hfactor_finalize(Cl.g, at(p, Cl.H64), at(p, Cl.H32), st));
+    CK(launch_vgalerkin(F.tr, at(p, F.V64), at(p, Cl.V64), at(p, Cl.V32), st));
+  }
+  Level& Lc = p->lv.back();
+  PROF(MCWIND_K_SETUP);
+  CK(launch_sep_expand64(Lc.g, at(p, Lc.H64), at(p, Lc.V64), at(p, Lc.C64), st));
+  CK(launch_stencil_finalize(Lc.g, at(p, Lc.C64), flagp(p), st));
+  return MCWIND_OK;
+}
+
+}  // namespace
 
 extern "C" int mcwind_rhs(mcwind_plan p, const double* u0, double* f, void* stream) {
   if (!p || !u0 || !f) return MCWIND_EINVAL;
@@ -746,7 +851,12 @@ extern "C" int mcwind_level_stencil(mcwind_plan p, int level, int precision, dou
   if (!out) return MCWIND_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const Grid& g = p->lv[level].g;
-  if (precision == MCWIND_PREC_F64)
+  const Level& L = p->lv[level];
+  if (p->sep && precision == MCWIND_PREC_F64)
+    CK(launch_sep_export<double>(g, at(p, L.H64), at(p, L.V64), out, st));
+  else if (p->sep)
+    CK(launch_sep_export<float>(g, at(p, L.H32), at(p, L.V32), out, st));
+  else if (precision == MCWIND_PREC_F64)
     CK(launch_stencil_export<double>(g, lv64(p, level).C, out, st));
   else
     CK(launch_stencil_export<float>(g, lv32(p, level).C, out, st));
@@ -755,7 +865,7 @@ extern "C" int mcwind_level_stencil(mcwind_plan p, int level, int precision, dou
 
 extern "C" int mcwind_level_residual(mcwind_plan p, int level, int precision, const double* x,
                                      const double* f, double* r, void* stream) {
-  CKR(check_level(p, level, precision));
+  CKR(check_level(p, level, precision, true));
   if (!x || !f || !r) return MCWIND_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const Grid& g = p->lv[level].g;
@@ -769,15 +879,42 @@ extern "C" int mcwind_level_residual(mcwind_plan p, int level, int precision, co
     Ptr32 P = lv32(p, level);
     CK(launch_std_to_split<float>(g, x, P.x, true, st));
     CK(launch_std_to_split<float>(g, f, P.f, true, st));
-    CK(launch_residual<float>(g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
+    if (p->sep)
+      CK(launch_residual_sep(g, nullptr, sep_h32(p, level), sep_v32(p, level), P.f, P.x, P.r, st));
+    else
+      CK(launch_residual<float>(g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
     CK(launch_split_to_std<float>(g, P.r, r, st));
+  }
+  return MCWIND_OK;
+}
+
+extern "C" int mcwind_level_residual_restrict(mcwind_plan p, int level, int precision,
+                                              const double* x, const double* f, double* fc,
+                                              void* stream) {
+  CKR(check_level(p, level, precision, true));
+  if (level + 1 >= (int)p->lv.size() || !x || !f || !fc) return MCWIND_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Grid& g = p->lv[level].g;
+  const Grid& gc = p->lv[level + 1].g;
+  if (precision == MCWIND_PREC_F64) {
+    Ptr64 P = lv64(p, level), Q = lv64(p, level + 1);
+    CK(launch_std_to_split<double>(g, x, P.x, true, st));
+    CK(launch_std_to_split<double>(g, f, P.f, true, st));
+    CKR(residual_restrict<double>(p, level, st));
+    CK(launch_split_to_std<double>(gc, Q.f, fc, st));
+  } else {
+    Ptr32 P = lv32(p, level), Q = lv32(p, level + 1);
+    CK(launch_std_to_split<float>(g, x, P.x, true, st));
+    CK(launch_std_to_split<float>(g, f, P.f, true, st));
+    CKR(residual_restrict<float>(p, level, st));
+    CK(launch_split_to_std<float>(gc, Q.f, fc, st));
   }
   return MCWIND_OK;
 }
 
 extern "C" int mcwind_level_smooth(mcwind_plan p, int level, int precision, double* x,
                                    const double* f, int sweeps, int direction, void* stream) {
-  CKR(check_level(p, level, precision));
+  CKR(check_level(p, level, precision, true));
   if (!x || !f || sweeps < 0) return MCWIND_EINVAL;
   if (direction != MCWIND_FORWARD && direction != MCWIND_BACKWARD) return MCWIND_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -859,6 +996,7 @@ extern "C" int mcwind_coarse_solve(mcwind_plan p, const double* f, double* x, vo
 extern "C" int mcwind_vcycle(mcwind_plan p, int precision, double* x, const double* f,
                              void* stream) {
   CKR(check_level(p, 0, precision));
+  if (p->sep && precision == MCWIND_PREC_F64) return MCWIND_EINVAL;
   if (!x || !f) return MCWIND_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const Grid& g = p->lv[0].g;

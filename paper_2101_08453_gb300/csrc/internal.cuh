@@ -113,12 +113,40 @@ __host__ __device__ inline void hcoarse(int coarsen, int Nf, int Nc, int I, int&
   wp = (f + 1 <= Nf - 2 && ((f + 1) & 1)) ? W(0.5) : W(0);
 }
 
+// Separable (column x layer) operator of a shift-form grid (MCWIND_OP_SEPARABLE).
+// On a terrain-following grid z = z_s(x, y) + zeta_k the element stiffness
+// is (h/2) Phat (x) m - Qhat (x) g - Qhat^T (x) g^T + (2/h) Rhat (x) kappa,
+// with Phat, Qhat, Rhat (4 x 4) depending on the column's terrain only and
+// m, g, kappa the fixed 1-D matrices of a linear element, so every level's
+// K_FF = sum_t H_t (x) V_t: four horizontal 9-point operators H_t over the
+// node columns and four vertical tridiagonal V_t over the layers, a form
+// the tensor-product Galerkin products of Eq. 7 keep.  Terms t: 0 = (H_P,
+// V_M), 1 = (H_Q, V_G), 2 = (H_Q^T, V_G^T), 3 = (H_R, V_K).
+//   horizontal factor q = 9 t + s2, s2 = (di+1) + 3 (dj+1): H_t(c, c + d) of
+//     column c; float64 as plain planes H64[q * PP + col], float32 in tiles of
+//     32 columns H32[hidx(col, q)];
+//   vertical factor 3 t + (dk+1) of layer k: V_t(k, k + dk), V[k * kVF + ...].
+// Couplings to fixed columns and to the top layer are zero.
+constexpr int kHF = 36;
+constexpr int kVF = 12;
+__host__ __device__ constexpr int64_t hidx(int64_t col, int q) {
+  return ((col >> 5) * kHF + q) * 32 + (col & 31);
+}
+
 struct Level {
   Grid g;
   int n_free;
   // device pointers into the workspace
   double* C64 = nullptr;   // kPlanes * g.total
   float* C32 = nullptr;
+  // separable form: horizontal factors (shared with the finer level when the
+  // transfer keeps the columns) and vertical factors
+  double* H64 = nullptr;
+  float* H32 = nullptr;
+  double* V64 = nullptr;
+  float* V32 = nullptr;
+  bool h_shared = false;
+  bool has_c64 = true;     // false: separable form on an intermediate level
   double *x64 = nullptr, *f64 = nullptr, *r64 = nullptr;
   float *x32 = nullptr, *f32 = nullptr, *r32 = nullptr;
   // host description of the transfer to the next level
@@ -134,6 +162,8 @@ struct mcwind_plan_s {
   double a[3];
   mcwind_options opt;
   int gs_rows = 4;                          // smoother thread-block height (tunable)
+  bool sep = false;                         // MCWIND_OP_SEPARABLE: float32 cycle on factors
+  int status_host = 0;                      // last device status word read
   bool in_batch = false;
   std::vector<mcw::Level> lv;
   // workspace layout (byte offsets) and sizes

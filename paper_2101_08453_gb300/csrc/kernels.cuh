@@ -136,4 +136,45 @@ cudaError_t launch_cg_start(const Grid& g, const double* r, double* rp, TP* pf, 
 cudaError_t launch_reduce_pairs(const double* partials, int n, double* out0, double* out1,
                                 cudaStream_t st);
 
+// ---- separable.cu: column x layer operator of a shift-form grid ----
+// flag |= 8 when X, Y depend on k or Z - Z(.,.,0) differs between columns
+cudaError_t launch_shift_check(int Nx, int Ny, int Nz, const double* X, const double* Y,
+                               const double* Z, int* flag, cudaStream_t st);
+// finest horizontal factors from the ground layer of X, Y, Z (standard
+// layout), fixed couplings zeroed, float32 tiles written; flag |= 1 on j2 <= 0
+cudaError_t launch_hfactors(const Grid& g, const double* X, const double* Y, const double* Z,
+                            const double* a, double* H64, float* H32, int* flag,
+                            cudaStream_t st);
+cudaError_t launch_hfactor_finalize(const Grid& g, double* H64, float* H32, cudaStream_t st);
+// one direction (0: x, 1: y) of Ph^T H Ph for the 4 terms (float64)
+cudaError_t launch_hgalerkin(int dim, const Grid& gin, const Grid& gout, const double* Hin,
+                             double* Hout, cudaStream_t st);
+// finest vertical factors from column (0, 0) of Z; Galerkin to the next level
+cudaError_t launch_vfactor0(int Nx, int Ny, int Nz, const double* Z, double* V64, float* V32,
+                            cudaStream_t st);
+cudaError_t launch_vgalerkin(const Transfer& tr, const double* Vf, double* Vc, float* Vc32,
+                             cudaStream_t st);
+// 27-point rows from float64 factors into a tiled float64 operator (planes 0..26)
+cudaError_t launch_sep_expand64(const Grid& g, const double* H64, const double* V64, double* C,
+                                cudaStream_t st);
+// rows from the factors in the standard layout [27][N] (T = double: float64
+// planes; T = float: float32 tiles)
+template <typename T>
+cudaError_t launch_sep_export(const Grid& g, const T* H, const T* V, double* out, cudaStream_t st);
+// float32 cycle on the factors: one Gauss-Seidel column group; the first group
+// of a forward sweep from x = 0; r = f - K x, or (fuse = the level's transfer,
+// vertical coarsening only) f_c = P^T (f - K x) on the coarse grid
+cudaError_t launch_gs_sep(const Grid& g, const float* H32, const float* V32, const float* f,
+                          float* x, int group, int up, int rows, cudaStream_t st);
+// the sweep with x and f staged through shared memory by bulk copies; a wait
+// that runs out sets bit 1 of *status
+cudaError_t launch_gs_sep_staged(const Grid& g, const float* H32, const float* V32,
+                                 const float* f, float* x, int group, int up, int* status,
+                                 cudaStream_t st);
+cudaError_t launch_gs_sep_zero_start(const Grid& g, const float* H32, const float* V32,
+                                     const float* f, float* x, int group, cudaStream_t st);
+cudaError_t launch_residual_sep(const Grid& g, const Transfer* fuse, const float* H32,
+                                const float* V32, const float* f, const float* x, float* out,
+                                cudaStream_t st);
+
 }  // namespace mcw

@@ -109,6 +109,7 @@ extern "C" void mcwind_default_options(mcwind_options* o) {
   o->u0_at = MCWIND_U0_NODES;
   o->element_arith = MCWIND_ARITH_DFLOAT;
   o->cycles_per_check = 0;
+  o->op_form = MCWIND_OP_STORED;
 }
 
 extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], double h1,
@@ -142,6 +143,8 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   if (o.u0_at != MCWIND_U0_NODES && o.u0_at != MCWIND_U0_CENTERS) return MCWIND_EINVAL;
   if (o.element_arith != MCWIND_ARITH_F64 && o.element_arith != MCWIND_ARITH_DFLOAT) return MCWIND_EINVAL;
   if (o.cycles_per_check < 0 || o.cycles_per_check > 8) return MCWIND_EINVAL;
+  if (o.op_form != MCWIND_OP_STORED && o.op_form != MCWIND_OP_SEPARABLE) return MCWIND_EINVAL;
+  if (o.op_form == MCWIND_OP_SEPARABLE && o.precision != MCWIND_PREC_MIXED) return MCWIND_EINVAL;
 
   std::vector<PlanLevel> H = hierarchy(nx, ny, nz, a, h1, h3, o.coarsen_rule, o.coarsest_max);
   if (H.empty() || !H.back().kmap.empty()) return MCWIND_EINVAL;
@@ -154,6 +157,7 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
   p->nx = nx; p->ny = ny; p->nz = nz;
   p->a[0] = a[0]; p->a[1] = a[1]; p->a[2] = a[2];
   p->opt = o;
+  p->sep = o.op_form == MCWIND_OP_SEPARABLE;
   const bool mixed = o.precision == MCWIND_PREC_MIXED;
   size_t off = 0;
   int max_blocks = 0;
@@ -164,8 +168,24 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
     L.hx = H[l].hx; L.hy = H[l].hy; L.kmap = H[l].kmap;
     if (l + 1 < H.size()) L.tr = make_transfer(L.hx, L.hy, L.g.Nz, L.kmap);
     const size_t t = (size_t)L.g.total;
-    L.C64 = (double*)off; off = align256(off + kPlanes * t * 8);
-    if (mixed) { L.C32 = (float*)off; off = align256(off + kPlanes * t * 4); }
+    // separable form: float64 operator on the finest and the coarsest level
+    // only, no float32 copy, factors per level (the horizontal ones shared
+    // with the finer level when its transfer keeps the columns)
+    L.has_c64 = !p->sep || l == 0 || l + 1 == H.size();
+    if (L.has_c64) { L.C64 = (double*)off; off = align256(off + kPlanes * t * 8); }
+    if (mixed && !p->sep) { L.C32 = (float*)off; off = align256(off + kPlanes * t * 4); }
+    if (p->sep) {
+      const Level* F = l > 0 ? &p->lv[l - 1] : nullptr;
+      if (F && !F->hx && !F->hy) {
+        L.H64 = F->H64; L.H32 = F->H32; L.h_shared = true;
+      } else {
+        const size_t cols = (size_t)L.g.PP;
+        L.H64 = (double*)off; off = align256(off + kHF * cols * 8);
+        L.H32 = (float*)off; off = align256(off + kHF * cols * 4);
+      }
+      L.V64 = (double*)off; off = align256(off + (size_t)kVF * L.g.Nz * 8);
+      L.V32 = (float*)off; off = align256(off + (size_t)kVF * L.g.Nz * 4);
+    }
     L.x64 = (double*)off; off = align256(off + t * 8);
     L.f64 = (double*)off; off = align256(off + t * 8);
     L.r64 = (double*)off; off = align256(off + t * 8);
@@ -191,9 +211,19 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
     if (outs.size() >= 3) tmpB = std::max(tmpB, outs[1]);
   }
   p->off_tmp = off;
-  // stage outputs in the tiled operator layout (28 slots per node, 27 used)
-  p->tmp_bytes = align256(kPlanes * tmpA * 8);
-  off = align256(off + p->tmp_bytes + kPlanes * tmpB * 8);
+  if (p->sep) {
+    // horizontal factors after the x stage of a transfer that halves both directions
+    size_t cols = 0;
+    for (size_t l = 0; l + 1 < p->lv.size(); ++l)
+      if (p->lv[l].hx && p->lv[l].hy)
+        cols = std::max(cols, (size_t)make_grid(p->lv[l + 1].g.Nx, p->lv[l].g.Ny, 1).PP);
+    p->tmp_bytes = align256(kHF * cols * 8);
+    off = align256(off + p->tmp_bytes);
+  } else {
+    // stage outputs in the tiled operator layout (28 slots per node, 27 used)
+    p->tmp_bytes = align256(kPlanes * tmpA * 8);
+    off = align256(off + p->tmp_bytes + kPlanes * tmpB * 8);
+  }
   p->n_coarse = (int)nc;
   p->off_dense = off; off = align256(off + 2 * (size_t)nc * nc * 8);
   p->off_cfree = off; off = align256(off + (size_t)nc * 4);

@@ -127,6 +127,33 @@ def test_planner_matches_hand_derived_aniso64(rule, key):
             assert got[name] == value, (l, name, got, want)
 
 
+def test_separable_form_needs_mixed_precision():
+    h3 = [5.0, 6.0, 7.0, 8.0]
+    with pytest.raises(m.MCWindError) as e:
+        m.mcwind_plan_create(64, 48, 4, (1, 1, 1), 30.0, h3,
+                             m.default_options(op_form=m.OP_SEPARABLE))
+    assert e.value.code == m.MCWIND_EINVAL
+    with pytest.raises(m.MCWindError):
+        m.mcwind_plan_create(64, 48, 4, (1, 1, 1), 30.0, h3,
+                             m.default_options(precision=m.PREC_MIXED, op_form=7))
+
+
+def test_separable_workspace_at_full_size():
+    """Memory per grid point (Sec. 1, requirement 3): at 3000 x 3000 x 15 the
+    separable form keeps the float64 operator of the finest level (for the
+    float64 residual) and drops the float32 copy and the stored coarse
+    operators: about half the stored form's workspace."""
+    h3 = synth.layer_thicknesses(15)
+    _, stored = m.mcwind_plan_create(3000, 3000, 15, (1, 1, 1), 30.0, h3,
+                                     m.default_options(precision=m.PREC_MIXED))
+    _, sep = m.mcwind_plan_create(3000, 3000, 15, (1, 1, 1), 30.0, h3,
+                                  m.default_options(precision=m.PREC_MIXED,
+                                                    op_form=m.OP_SEPARABLE))
+    nodes = 3001 * 3001 * 16
+    assert sep < 0.6 * stored, (sep, stored)
+    assert sep / nodes < 420, sep / nodes   # bytes per node, all levels
+
+
 def test_cg_workspace_is_larger():
     h3 = [5.0, 6.0, 7.0, 8.0]
     _, ws0 = m.mcwind_plan_create(64, 48, 4, (1, 1, 1), 30.0, h3)
