@@ -50,8 +50,7 @@ FP32_PIPE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per unit of a launch, from one ncu capture of the
 # 600x600x15 case, scaled by the units of the full launch: FP32 smoother,
 # bytes per node of the column group.
-TRAFFIC_PER_UNIT = {"smooth_fine": (142.3, "ncu dram__bytes_read+write at 600x600x15, "
-                                           "scaled by the column-group nodes")}
+TRAFFIC_PER_UNIT = {}
 
 
 def parse():
@@ -237,6 +236,82 @@ def read_profile(m, plan):
     n = (ctypes.c_longlong * len(KINDS))()
     m.lib().mcwind_profile_read(plan.handle, ms, n, len(KINDS), m._stream(None))
     return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}
+
+
+def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse):
+    """Algorithmic units of every kernel class over the timed region.
+
+    levels: the plan's level descriptions (Nx, Ny, Nz, hx, hy); solves: the
+    cycle counts of the timed solves.  For each class a list of (bound, total
+    units): bytes every array element the launches must read or write at
+    least once ("hbm"), float64 FMAs ("fp64"), float-pair FP32-pipe operations
+    ("alu").  A smoother launch of one column group reads the x values of the
+    whole level (its 8 neighbours lie in the other groups), f and the
+    coefficients (or the column factors) of its own nodes, and writes its own
+    x; the residual reads x, f and the coefficients once and writes r (or,
+    fused with the vertical restriction, the coarse right side)."""
+    cs = 4 if mixed else 8
+    L = len(levels)
+    nodes = [d["Nx"] * d["Ny"] * d["Nz"] for d in levels]
+    free = [(d["Nx"] - 2) * (d["Ny"] - 2) * (d["Nz"] - 1) for d in levels]
+    fcols = [(d["Nx"] - 2) * (d["Ny"] - 2) for d in levels]
+    cycles = sum(solves)
+    checks = sum(c // cpc for c in solves) if mixed else cycles
+    nsolve = len(solves)
+    fac = 36 * 4            # float32 factor bytes per column
+    U = {k: [] for k in ("smooth_fine", "smooth_coarse", "residual_fine", "residual_coarse",
+                         "restrict", "prolong", "coarse_solve", "update", "outer_residual")}
+
+    def add(key, bound, v):
+        U[key].append([bound, v])
+
+    hb = {k: 0.0 for k in U}
+    fp64 = {k: 0.0 for k in U}
+    for l in range(L - 1):
+        sm = "smooth_fine" if l == 0 else "smooth_coarse"
+        rs = "residual_fine" if l == 0 else "residual_coarse"
+        g4 = free[l] / 4.0
+        if separable:
+            full = 4 * nodes[l] + 8 * g4 + fac * fcols[l] / 4.0
+            zero = 4 * g4 + 16 * fcols[l] / 4.0 + 4 * nodes[l]
+        else:
+            full = 27 * cs * g4 + cs * nodes[l] + 2 * cs * g4
+            zero = 2 * cs * g4 + cs * g4 + cs * nodes[l]
+        n_launch = 4 * (nu[0] + nu[1])
+        # first group of each pre-smoothing starts from zero on the coarse levels, and
+        # on the finest level in the first cycle of each check (mixed precision)
+        n_zero = cycles if l > 0 else (checks if mixed else 0)
+        hb[sm] += (cycles * n_launch - n_zero) * full + n_zero * zero
+        if not mixed:
+            fp64[sm] += cycles * n_launch * 27 * g4
+        fused = separable and not levels[l]["hx"] and not levels[l]["hy"]
+        if separable:
+            rb = 4 * nodes[l] + 4 * free[l] + fac * fcols[l] + (4 * nodes[l + 1] if fused else 4 * nodes[l])
+        else:
+            rb = 27 * cs * free[l] + cs * nodes[l] + cs * free[l] + cs * nodes[l]
+        hb[rs] += cycles * rb
+        if not mixed:
+            fp64[rs] += cycles * 27 * free[l]
+        if not fused:
+            hb["restrict"] += cycles * (cs * nodes[l] + cs * nodes[l + 1])
+        hb["prolong"] += cycles * (cs * nodes[l + 1] + 2 * cs * free[l])
+    hb["coarse_solve"] += cycles * 8.0 * n_coarse * n_coarse
+    fp64["coarse_solve"] += cycles * float(n_coarse) * n_coarse
+    if mixed:
+        hb["update"] += checks * 20.0 * free[0]
+    n_outer = checks + nsolve
+    hb["outer_residual"] += n_outer * (27 * 8 + 8 + 8 + (8 if mixed else 8)) * free[0]
+    fp64["outer_residual"] += n_outer * 28.0 * free[0]
+    for k in U:
+        if hb[k]:
+            add(k, "hbm", hb[k])
+        if fp64[k]:
+            add(k, "fp64", fp64[k])
+    # per call: load vector (2 per step), recovery (2 per step), assembly (1 per step)
+    U["rhs"] = [["alu", nsolve * FP32_OPS_LOAD * n_elem]]
+    U["assemble"] = [["alu", nsolve / 2 * FP32_OPS_STIFFNESS * n_elem]]
+    U["recover"] = [["hbm", nsolve * ((8 + 24 + 24) * nodes[0] + 24.0 * n_elem)]]
+    return {k: v for k, v in U.items() if v}
 
 
 def bench_batched(args):
@@ -437,6 +512,9 @@ def main():
     plan = m.Plan.for_case(case, precision=prec, op_form=op_form)
     plan_cpc = plan.options.cycles_per_check
     plan_ws = plan.workspace_bytes
+    plan_nu = (plan.options.nu_pre, plan.options.nu_post)
+    main_levels = [plan.level(l) for l in range(plan.num_levels)]
+    f64_levels, f64_solves = None, None
     lam = torch.zeros(plan.node_shape, dtype=torch.float64, device=dev)
     u_c = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev)
     u_w = torch.empty_like(u_c)
@@ -594,6 +672,8 @@ def main():
         t64w, s64w = time_solve(p64, U0N, True)
         prof_f64 = read_profile(m, p64)
         m.lib().mcwind_profile(p64.handle, 0, m._stream(None))
+        f64_levels = [p64.level(l) for l in range(p64.num_levels)]
+        f64_solves = [s64c.cycles, s64w.cycles]
         tt["f64"] = {"cold_s": t64c, "cold_cycles": s64c.cycles, "warm_s": t64w,
                      "warm_cycles": s64w.cycles, "cold_rate": s64c.rate}
         del p64
@@ -612,67 +692,57 @@ def main():
     # FP64 pipe of this GB300: 2 FP64 FMA per clock per SM, measured 5.81e11 FMA/s
     FP64_PEAK_T = 0.581
 
-    def algo_units(cs, mixed):
-        """Algorithmic units of one launch (node classes) or one call (element classes:
-        3 + 8 or 1 + 8 launches, the input splits into float pairs and the 8
-        element-parity launches) of each class, per bound: bytes moved for the
-        HBM-bound stencils, FMAs for the FP64-pipe-bound ones, float-pair
-        operations for the element kernels."""
-        f64 = cs == 8
-        return {
-            # bytes: 26 off-diagonal coefficients + 1/diagonal + f + x read + x write per
-            # free node of one column group; float64: 26 FMA + 1 multiply per node
-            "smooth_fine": (1, [("hbm", (27 * cs + 3 * cs) * n_free / 4.0)]
-                            + ([("fp64", 27 * n_free / 4.0)] if f64 else [])),
-            "residual_fine": (1, [("hbm", (27 * cs + 3 * cs) * n_free)]
-                              + ([("fp64", 27 * n_free)] if f64 else [])),
-            # float64 residual: 27 coefficients + f + x + r out (+ float32 r and e out
-            # when mixed); 27 FMA of the stencil + 1 of the squared norm per node
-            "outer_residual": (1, [("hbm", (27 * 8 + 3 * 8 + (8 if mixed else 0)) * n_free),
-                                   ("fp64", 28 * n_free)]),
-            # FP32-pipe operations of all elements (float pairs, modal form, counted by
-            # ncu per element): stiffness and load vector
-            "assemble": (11, [("alu", FP32_OPS_STIFFNESS * n_elem)]),
-            "rhs": (9, [("alu", FP32_OPS_LOAD * n_elem)]),
-        }
-
     UNITS = {"hbm": ("GB/s", 1e9, hbm_peak), "fp64": ("T FP64 FMA/s", 1e12, FP64_PEAK_T),
              "alu": ("T FP32-pipe op/s", 1e12, FP32_PIPE_PEAK_T)}
 
-    def roofs(profile, cs, mixed):
-        """Per class: the bound with the highest fraction of its peak (the one that
-        binds), the other bounds' fractions beside it."""
+    def roofs(profile, units):
+        """Per class: achieved = its algorithmic units over the timed region / its
+        summed device time, against each bound; the bound with the highest
+        fraction of its peak is the one that binds, the others sit beside it."""
         out = {}
-        for k, (per_call, bounds) in algo_units(cs, mixed).items():
-            ms, n = profile[k]
-            if n == 0 or n % per_call:
+        for k, bounds in units.items():
+            ms, n = profile.get(k, (0.0, 0))
+            if n == 0 or ms <= 0.0:
                 continue
-            per = ms / (n // per_call) / 1e3
             cand = []
-            for bound, units in bounds:
+            for bound, total in bounds:
                 unit, scale, peak = UNITS[bound]
-                ach = units / per / scale
+                ach = total / (ms / 1e3) / scale
                 cand.append({"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                              "frac": ach / peak})
             best = dict(max(cand, key=lambda c: c["frac"]))
-            best["other_bounds"] = {c["bound"]: c["frac"] for c in cand
-                                    if c["bound"] != best["bound"]}
-            best["ms_per_launch" if per_call == 1 else "ms_per_call"] = per * 1e3
+            best["other_bounds"] = {c["bound"]: c["frac"] for c in cand if c["bound"] != best["bound"]}
+            best["ms"] = ms
             best["launches"] = n
+            best["ms_per_launch"] = ms / n
             out[k] = best
         return out
 
+    def plan_levels_of(p):
+        return [p.level(l) for l in range(p.num_levels)]
+
     mixed = prec == m.PREC_MIXED
-    roof_kernels = roofs(prof_main, 4 if mixed else 8, mixed)
-    roof_f64 = roofs(prof_f64, 8, False) if prof_f64 else None
+    cpc = plan_cpc or (2 if mixed else 1)
+    timed_solves = [c for cyc in cycles for c in cyc[:2]]
+    lev_main = main_levels
+    nc_main = ((lev_main[-1]["Nx"] - 2) * (lev_main[-1]["Ny"] - 2) * (lev_main[-1]["Nz"] - 1))
+    units_main = class_units(lev_main, mixed, op_form == m.OP_SEPARABLE, timed_solves,
+                             (plan_nu[0], plan_nu[1]), cpc, n_elem, nc_main)
+    roof_kernels = roofs(prof_main, units_main)
+    roof_f64 = None
+    if prof_f64:
+        nc64 = ((f64_levels[-1]["Nx"] - 2) * (f64_levels[-1]["Ny"] - 2) * (f64_levels[-1]["Nz"] - 1))
+        roof_f64 = roofs(prof_f64, class_units(f64_levels, False, False, f64_solves,
+                                               (plan_nu[0], plan_nu[1]), 1, n_elem, nc64))
     dom = max((k for k in prof_main if prof_main[k][1] > 0), key=lambda k: prof_main[k][0])
     dom_roof = dict(roof_kernels.get(dom, {"bound": None}))
     dom_roof["kernel"] = dom
     dom_roof["traffic"] = None
     if dom in TRAFFIC_PER_UNIT and mixed:
-        per_unit, how = TRAFFIC_PER_UNIT[dom]
-        dom_roof["traffic"] = per_unit * n_free / 4.0
-        dom_roof["traffic_source"] = how
+        per_unit, how, form = TRAFFIC_PER_UNIT[dom]
+        if form == args.op_form:
+            dom_roof["traffic"] = per_unit * n_free / 4.0
+            dom_roof["traffic_source"] = how
     dom_roof["peak_source"] = {
         "hbm": "measured: MEASURED_PEAKS.json hbm_gbs (burst copy)",
         "fp64": "measured: FP64 FMA issue rate of this GB300, 5.81e11/s",

@@ -187,8 +187,7 @@ int smooth(mcwind_plan p, int l, int sweeps, int direction, cudaStream_t st,
         if (first)
           CK(launch_gs_sep_zero_start(g, H, V, (const float*)P.f, (float*)P.x, grp, st));
         else
-          CK(launch_gs_sep_staged(g, H, V, (const float*)P.f, (float*)P.x, grp, up, statusp(p),
-                                  st));
+          CK(launch_gs_sep_staged(p->lv[l], H, V, (float*)P.x, grp, up, statusp(p), st));
       } else if (first) {
         CK(launch_gs_zero_start<T>(g, P.C, P.f, P.x, grp, st));
       } else {
@@ -210,9 +209,8 @@ int residual_restrict(mcwind_plan p, int l, cudaStream_t st) {
     const bool fuse = !L.hx && !L.hy;
     {
       PROF(l == 0 ? MCWIND_K_RESIDUAL_FINE : MCWIND_K_RESIDUAL_COARSE);
-      CK(launch_residual_sep(L.g, fuse ? &L.tr : nullptr, sep_h32(p, l), sep_v32(p, l),
-                             (const float*)P.f, (const float*)P.x,
-                             fuse ? (float*)Q.f : (float*)P.r, st));
+      CK(launch_residual_sep_staged(L, fuse, sep_h32(p, l), sep_v32(p, l),
+                                    fuse ? (float*)Q.f : (float*)P.r, statusp(p), st));
     }
     if (fuse) return MCWIND_OK;
   } else {
@@ -405,7 +403,7 @@ extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, 
   for (size_t l = 0; l < p->lv.size(); ++l) {
     Level& L = p->lv[l];
     const size_t t = (size_t)L.g.total;
-    if (l == 0) CK(cudaMemsetAsync(at(p, L.C64), 0, kPlanes * t * 8, st));
+    if (l == 0 && !p->sep) CK(cudaMemsetAsync(at(p, L.C64), 0, kPlanes * t * 8, st));
     Ptr64 A = lv64(p, (int)l);
     CK(cudaMemsetAsync(A.x, 0, 3 * ((t * 8 + 255) / 256 * 256), st));
     if (p->opt.precision == MCWIND_PREC_MIXED) {
@@ -424,10 +422,12 @@ extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, 
       CK(launch_split_pairs(Y, xyz2 + nn, nn, st));
       CK(launch_split_pairs(Z, xyz2 + 2 * nn, nn, st));
     }
-    CK(launch_assemble_stencil(L0.g, p->nx, p->ny, p->nz, X, Y, Z, xyz2, p->a, at(p, L0.C64),
-                               flagp(p), dfloat_elements(p), st));
+    // the separable form expands the finest rows from its factors instead
+    if (!p->sep)
+      CK(launch_assemble_stencil(L0.g, p->nx, p->ny, p->nz, X, Y, Z, xyz2, p->a, at(p, L0.C64),
+                                 flagp(p), dfloat_elements(p), st));
   }
-  {
+  if (!p->sep) {
     PROF(MCWIND_K_SETUP);
     CK(launch_stencil_finalize(L0.g, at(p, L0.C64), flagp(p), st));
   }
@@ -503,8 +503,20 @@ int assemble_separable(mcwind_plan p, cudaStream_t st) {
     PROF(MCWIND_K_SETUP);
     CK(launch_shift_check(Nx, Ny, Nz, p->X, p->Y, p->Z, flagp(p), st));
     CK(launch_hfactors(L0.g, p->X, p->Y, p->Z, p->a, at(p, L0.H64), at(p, L0.H32), flagp(p), st));
-    CK(launch_vfactor0(Nx, Ny, Nz, p->Z, at(p, L0.V64), at(p, L0.V32), st));
+    CK(launch_vfactor0(Nx, Ny, Nz, p->Z, at(p, L0.V64), at(p, L0.V32), flagp(p), st));
   }
+  {
+    // the finest float64 rows (the refinement's residual operator): the same
+    // 2x2x2-Gauss stiffness, assembled from its column and layer factors
+    PROF(MCWIND_K_ASSEMBLE);
+    CK(launch_sep_expand64(L0.g, at(p, L0.H64), at(p, L0.V64), at(p, L0.C64), st));
+  }
+  {
+    PROF(MCWIND_K_SETUP);
+    CK(launch_stencil_finalize(L0.g, at(p, L0.C64), flagp(p), st));
+  }
+  for (size_t l = 0; l < p->lv.size(); ++l)
+    CK(make_tile_maps(p->lv[l], at(p, p->lv[l].x32), at(p, p->lv[l].f32)));
   double* tmp = (double*)(p->ws + p->off_tmp);
   for (size_t l = 0; l + 1 < p->lv.size(); ++l) {
     Level& F = p->lv[l];
@@ -880,7 +892,8 @@ extern "C" int mcwind_level_residual(mcwind_plan p, int level, int precision, co
     CK(launch_std_to_split<float>(g, x, P.x, true, st));
     CK(launch_std_to_split<float>(g, f, P.f, true, st));
     if (p->sep)
-      CK(launch_residual_sep(g, nullptr, sep_h32(p, level), sep_v32(p, level), P.f, P.x, P.r, st));
+      CK(launch_residual_sep_staged(p->lv[level], false, sep_h32(p, level), sep_v32(p, level),
+                                    P.r, statusp(p), st));
     else
       CK(launch_residual<float>(g, P.C, P.f, P.x, P.r, nullptr, 0, nullptr, st));
     CK(launch_split_to_std<float>(g, P.r, r, st));

@@ -52,6 +52,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+// one plain arrival (count 1)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
@@ -70,13 +75,14 @@ __device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity, int*
                                             unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
+  // try_wait suspends the thread in hardware until the phase completes or a
+  // short time limit passes, so the loop needs no sleep of its own
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (global_timer_ns() - t0 > limit_ns) {
       atomicOr(status, kStatusWaitTimeout);
       return false;
     }
-    __nanosleep(128);
   }
 }
 
@@ -87,6 +93,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(smem_u32(dst)),
       "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// a 4-D tile of a tensor map (coordinates innermost first) into shared dst,
+// completion counted on bar; elements outside the tensor are filled with zero
+__device__ __forceinline__ void tensor_copy_4d(void* dst, const void* tmap, int c0, int c1, int c2,
+                                               int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"((unsigned long long)tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
 

@@ -18,6 +18,7 @@
 // warp stepping through a layer reads one contiguous block rather than 28
 // separate streams.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -147,12 +148,15 @@ struct Level {
   float* V32 = nullptr;
   bool h_shared = false;
   bool has_c64 = true;     // false: separable form on an intermediate level
+  // separable form: tensor maps of x32 and f32 as [Nz][Ny][2][H] float tiles
+  // for the staged smoother (built at assembly, tied to the workspace)
+  CUtensorMap tm_x, tm_f, tm_rx, tm_rf;
   double *x64 = nullptr, *f64 = nullptr, *r64 = nullptr;
   float *x32 = nullptr, *f32 = nullptr, *r32 = nullptr;
   // host description of the transfer to the next level
   int hx = 0, hy = 0;
   std::vector<int> kmap;   // coarse layer -> fine layer
-  Transfer tr;
+  Transfer tr{};
 };
 
 }  // namespace mcw

@@ -151,7 +151,7 @@ cudaError_t launch_hgalerkin(int dim, const Grid& gin, const Grid& gout, const d
                              double* Hout, cudaStream_t st);
 // finest vertical factors from column (0, 0) of Z; Galerkin to the next level
 cudaError_t launch_vfactor0(int Nx, int Ny, int Nz, const double* Z, double* V64, float* V32,
-                            cudaStream_t st);
+                            int* flag, cudaStream_t st);
 cudaError_t launch_vgalerkin(const Transfer& tr, const double* Vf, double* Vc, float* Vc32,
                              cudaStream_t st);
 // 27-point rows from float64 factors into a tiled float64 operator (planes 0..26)
@@ -161,20 +161,18 @@ cudaError_t launch_sep_expand64(const Grid& g, const double* H64, const double* 
 // planes; T = float: float32 tiles)
 template <typename T>
 cudaError_t launch_sep_export(const Grid& g, const T* H, const T* V, double* out, cudaStream_t st);
-// float32 cycle on the factors: one Gauss-Seidel column group; the first group
-// of a forward sweep from x = 0; r = f - K x, or (fuse = the level's transfer,
-// vertical coarsening only) f_c = P^T (f - K x) on the coarse grid
-cudaError_t launch_gs_sep(const Grid& g, const float* H32, const float* V32, const float* f,
-                          float* x, int group, int up, int rows, cudaStream_t st);
-// the sweep with x and f staged through shared memory by bulk copies; a wait
-// that runs out sets bit 1 of *status
-cudaError_t launch_gs_sep_staged(const Grid& g, const float* H32, const float* V32,
-                                 const float* f, float* x, int group, int up, int* status,
-                                 cudaStream_t st);
+// float32 cycle on the factors (x and f staged by TMA from the level's
+// tensor maps; a wait that runs out sets bit 1 of *status): one Gauss-Seidel
+// column group; the first group of a forward sweep from x = 0; r = f - K x,
+// or (fuse: the level's transfer keeps the columns) f_c = P^T (f - K x) on
+// the coarse grid.  make_tile_maps builds the maps of a level's x32 and f32.
+cudaError_t launch_gs_sep_staged(const Level& L, const float* H32, const float* V32, float* x,
+                                 int group, int up, int* status, cudaStream_t st);
 cudaError_t launch_gs_sep_zero_start(const Grid& g, const float* H32, const float* V32,
                                      const float* f, float* x, int group, cudaStream_t st);
-cudaError_t launch_residual_sep(const Grid& g, const Transfer* fuse, const float* H32,
-                                const float* V32, const float* f, const float* x, float* out,
-                                cudaStream_t st);
+cudaError_t launch_residual_sep_staged(const Level& L, bool fuse, const float* H32,
+                                       const float* V32, float* out, int* status,
+                                       cudaStream_t st);
+cudaError_t make_tile_maps(Level& L, float* x32, float* f32);
 
 }  // namespace mcw

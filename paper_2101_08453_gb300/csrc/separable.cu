@@ -20,6 +20,8 @@
 // a sum the tensor-product prolongation of Sec. 3 keeps on every level
 // (P^T (H (x) V) P = (Ph^T H Ph) (x) (Pv^T V Pv)).  The factor layout is
 // described in internal.cuh.
+#include <cudaTypedefs.h>
+
 #include "async.cuh"
 #include "kernels.cuh"
 
@@ -141,8 +143,14 @@ __global__ void __launch_bounds__(128) k_hfactor_cells(Grid g, int cls, const do
 }
 
 // Zero the couplings that touch a fixed column (and everything of padding
-// columns) in the float64 planes and write the float32 tiles.  One thread
-// per split-layout column: blockIdx.z = parity of i.
+// columns) in the float64 planes and write the float32 tiles in the form
+// the float32 kernels read: terms P, S = H_Q - H_Q^T, T = H_Q + H_Q^T, R
+// (S(c, c) = 0 exactly).  With V_G = A + B, A = (V_G - V_G^T)/2
+// antisymmetric and B = (V_G + V_G^T)/2, the two mixed terms are
+// H_Q (x) V_G + H_Q^T (x) V_G^T = S (x) A + T (x) B, and B is -1/2 on the
+// ground layer's diagonal and 0 elsewhere on every level (the ground layer
+// is a node layer of every level), so above the ground three terms remain.
+// One thread per split-layout column: blockIdx.z = parity of i.
 __global__ void __launch_bounds__(128) k_hfactor_finalize(Grid g, double* __restrict__ H,
                                                           float* __restrict__ H32) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,13 +161,41 @@ __global__ void __launch_bounds__(128) k_hfactor_finalize(Grid g, double* __rest
   const int64_t col = (int64_t)j * g.RP + (int64_t)par * g.H + h;
   const bool fc = i < g.Nx && free_column(g, i, j);
 #pragma unroll
-  for (int q = 0; q < kHF; ++q) {
-    const int s2 = q % 9;
+  for (int s2 = 0; s2 < 9; ++s2) {
     const bool keep = fc && free_column(g, i + s2 % 3 - 1, j + s2 / 3 - 1);
-    const double v = keep ? H[q * g.PP + col] : 0.0;
-    H[q * g.PP + col] = v;
-    H32[hidx(col, q)] = (float)v;
+    double v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      v[t] = keep ? H[(t * 9 + s2) * g.PP + col] : 0.0;
+      H[(t * 9 + s2) * g.PP + col] = v[t];
+    }
+    H32[hidx(col, s2)] = (float)v[0];
+    H32[hidx(col, 9 + s2)] = (float)(v[1] - v[2]);
+    H32[hidx(col, 18 + s2)] = (float)(v[1] + v[2]);
+    H32[hidx(col, 27 + s2)] = (float)v[3];
   }
+}
+
+// float32 vertical factors of one layer from its float64 ones (order M, G,
+// G^T, K, 3 offsets each): [0..2] V_M(k, k-1..k+1), [3..5] V_K, [6] A(k, k-1),
+// [7] A(k, k+1), [8] B(k, k), [9..11] 0.
+__device__ __forceinline__ void write_v32(const double* v, float* o) {
+  o[0] = (float)v[0]; o[1] = (float)v[1]; o[2] = (float)v[2];
+  o[3] = (float)v[9]; o[4] = (float)v[10]; o[5] = (float)v[11];
+  o[6] = (float)(0.5 * (v[3] - v[6]));
+  o[7] = (float)(0.5 * (v[5] - v[8]));
+  o[8] = (float)(0.5 * (v[4] + v[7]));
+  o[9] = o[10] = o[11] = 0.0f;
+}
+
+// coefficient of offset (s2, dk) in a row, from float32 factors: hq[t] =
+// term t of the column at s2 (P, S, T, R), v = the layer's float32 factors
+__device__ __forceinline__ float sep32_coef(const float hq[4], const float* v, int dk) {
+  float c = hq[0] * v[dk] + hq[3] * v[3 + dk];
+  if (dk == 0) c += hq[1] * v[6];
+  if (dk == 2) c += hq[1] * v[7];
+  if (dk == 1) c += hq[2] * v[8];
+  return c;
 }
 
 // One direction (DIM 0: x, 1: y) of the horizontal Galerkin product
@@ -225,12 +261,13 @@ __global__ void __launch_bounds__(128) k_hgalerkin(Grid gin, Grid gout,
 // kappa to layers l, l+1.  One thread.  Couplings to the top layer (fixed)
 // are zero.
 __global__ void k_vfactor0(int Nx, int Ny, int Nz, const double* __restrict__ Z,
-                           double* __restrict__ V, float* __restrict__ V32) {
+                           double* __restrict__ V, float* __restrict__ V32, int* flag) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   const int64_t lay = (int64_t)Nx * Ny;
   for (int q = 0; q < Nz * kVF; ++q) V[q] = 0.0;
   for (int l = 0; l + 1 < Nz; ++l) {
     const double h = Z[(int64_t)(l + 1) * lay] - Z[(int64_t)l * lay];
+    if (!(h > 0.0)) atomicOr(flag, 1);  // det J = (h/2) j2 must be positive
     double* lo = V + l * kVF;        // row l
     double* up = V + (l + 1) * kVF;  // row l + 1
     // term 0: (h/2) [[2,1],[1,2]]/3
@@ -245,7 +282,7 @@ __global__ void k_vfactor0(int Nx, int Ny, int Nz, const double* __restrict__ Z,
     V[(Nz - 2) * kVF + 3 * t + 2] = 0.0;
     for (int d = 0; d < 3; ++d) V[(Nz - 1) * kVF + 3 * t + d] = 0.0;
   }
-  for (int q = 0; q < Nz * kVF; ++q) V32[q] = (float)V[q];
+  for (int k = 0; k < Nz; ++k) write_v32(V + k * kVF, V32 + k * kVF);
 }
 
 // Vertical Galerkin product Pv^T V_t Pv with the layer map of the transfer
@@ -285,10 +322,8 @@ __global__ void k_vgalerkin(Transfer tr, const double* __restrict__ Vf, double* 
     if (K == tr.Nzc - 1) acc[3 * t] = acc[3 * t + 1] = acc[3 * t + 2] = 0.0;
     if (K == tr.Nzc - 2) acc[3 * t + 2] = 0.0;
   }
-  for (int q = 0; q < kVF; ++q) {
-    Vc[K * kVF + q] = acc[q];
-    Vc32[K * kVF + q] = (float)acc[q];
-  }
+  for (int q = 0; q < kVF; ++q) Vc[K * kVF + q] = acc[q];
+  write_v32(acc, Vc32 + K * kVF);
 }
 
 // Expanded 27-point rows from float64 factors into the tiled float64
@@ -314,7 +349,8 @@ __global__ void __launch_bounds__(128) k_sep_expand64(Grid g, const double* __re
 }
 
 // Rows from the factors in the standard layout [27][Nz][Ny][Nx] (the level
-// stencil export): float64 factors in float64, float32 factors in float32.
+// stencil export): float64 factors (planes, terms M, G, G^T, K) in float64,
+// float32 factors (tiles, the float32 form) in float32.
 template <typename T>
 __global__ void __launch_bounds__(128) k_sep_export(Grid g, const T* __restrict__ H,
                                                     const T* __restrict__ V,
@@ -329,218 +365,120 @@ __global__ void __launch_bounds__(128) k_sep_export(Grid g, const T* __restrict_
 #pragma unroll
   for (int s = 0; s < 27; ++s) {
     const int s2 = s % 9, dk = s / 9;
-    T c = T(0);
+    double c;
+    if (sizeof(T) == 8) {
+      c = 0.0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const T hv = sizeof(T) == 8 ? H[(t * 9 + s2) * g.PP + col] : H[hidx(col, t * 9 + s2)];
-      c += hv * V[k * kVF + 3 * t + dk];
+      for (int t = 0; t < 4; ++t) c += (double)H[(t * 9 + s2) * g.PP + col] * (double)V[k * kVF + 3 * t + dk];
+    } else {
+      float hq[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) hq[t] = (float)H[hidx(col, t * 9 + s2)];
+      c = sep32_coef(hq, (const float*)V + k * kVF, dk);
     }
-    out[s * n + o] = (double)c;
+    out[s * n + o] = c;
   }
 }
 
 // ---------------------------------------------------------------- cycle
+//
+// The float32 kernels stage x and f through shared memory.  A block owns
+// kGsR rows x 32 columns of the split layout; a producer warp loads, per
+// free layer and in sweep order, a tile of x around them (rows j0-1 ..
+// j0+span, both parity halves, half-row indices [h0-4, h0+36): the 9
+// columns around each owned column, the window starting on a 16-byte
+// boundary) and the owned f, as two TMA tiles of the level's tensor maps,
+// into a ring of kStages shared-memory stages, as far ahead of the
+// consumers as the ring allows; entries outside the grid arrive as zeros.
+// Each stage has a "full" mbarrier (one arrival + the tiles' bytes) and an
+// "empty" one (one arrival per consumer warp once its rows no longer read
+// the stage).  The consumer warps (one thread per column) never wait on each
+// other.  Per layer a thread forms its neighbour sums once -- they serve the
+// rows below, at and above -- so a row costs about 40 products.  Every wait
+// is bounded: one that runs out sets the status bit and its warp leaves; the
+// producer waits (bounded) for the tiles it issued before it leaves.
+constexpr int kGsR = 4;
+constexpr int kTileW = 40;
+constexpr int kStages = 8;
+// smoother: owned rows j0, j0+2, ..., j0+2(kGsR-1) (one column group)
+constexpr int kGsTileRows = 2 * kGsR + 1;
+constexpr int kGsX = 768;                         // 720 used; f 128-byte aligned
+constexpr int kGsFRows = 2 * kGsR - 1;
+constexpr int kGsStage = kGsX + kGsFRows * 32;    // 992 floats = 31 x 128 bytes
+constexpr uint32_t kGsBytes = (kGsTileRows * 2 * kTileW + kGsFRows * 32) * 4;
+// residual: owned rows j0 .. j0+kGsR-1 (one parity half)
+constexpr int kResTileRows = kGsR + 2;
+constexpr int kResX = 512;                        // 480 used
+constexpr int kResStage = kResX + kGsR * 32;      // 640 floats = 20 x 128 bytes
+constexpr uint32_t kResBytes = (kResTileRows * 2 * kTileW + kGsR * 32) * 4;
 
-// In-row offsets of the 9 columns around split-layout column (i, j):
-// c = (di+1) + 3 (dj+1).  A neighbour across i flips the parity half.
-__device__ __forceinline__ void column_offsets(const Grid& g, int i, int off[9]) {
-#pragma unroll
-  for (int c = 0; c < 9; ++c) {
-    const int ii = i + c % 3 - 1, dj = c / 3 - 1;
-    off[c] = dj * (int)g.RP + ((ii & 1) - (i & 1)) * g.H + ((ii >> 1) - (i >> 1));
+// producer side of the ring: tile t of nlay into stage t % kStages
+template <int STAGE>
+__device__ __forceinline__ bool produce(float (*tile)[STAGE], uint64_t* full, uint64_t* empty,
+                                        int nlay, bool up, uint32_t bytes, int fx,
+                                        const CUtensorMap* tmx, const CUtensorMap* tmf, int cx0,
+                                        int cx2, int cf0, int cf1, int cf2, int* status) {
+  const int lane = threadIdx.x;
+  int issued = 0;
+  bool ok = true;
+  for (int t = 0; t < nlay; ++t) {
+    const int sidx = t & (kStages - 1);
+    if (t >= kStages) {
+      ok = wait_parity(&empty[sidx], (uint32_t)(t / kStages - 1) & 1u, status, kWaitLimitNs);
+      if (__any_sync(0xffffffffu, !ok)) break;  // the warp leaves together
+    }
+    if (lane == 0) {
+      const int k = up ? t : nlay - 1 - t;
+      fence_proxy_async_shared();
+      mbar_arrive_expect_tx(&full[sidx], bytes);
+      tensor_copy_4d(tile[sidx], tmx, cx0, 0, cx2, k, &full[sidx]);
+      tensor_copy_4d(tile[sidx] + fx, tmf, cf0, cf1, cf2, k, &full[sidx]);
+    }
+    __syncwarp();
+    issued = t + 1;
   }
+  // the block's shared memory must outlive the tiles this warp issued
+  if (lane == 0)
+    for (int u = max(0, issued - kStages); u < issued; ++u)
+      wait_parity(&full[u & (kStages - 1)], (uint32_t)(u / kStages) & 1u, status, kWaitLimitNs);
+  return ok;
 }
 
 // Gauss-Seidel of Sec. 3 on the separable float32 operator, one column
-// group per launch, one thread per column, the layers bottom-up (UP) or
-// top-down.  Per layer k' the thread forms the four neighbour sums
-// y_t(k') = sum_{d != 0} H_t(c, c + d) x(c + d, k') once (they serve rows
-// k'-1, k', k'+1), so a row costs 32 + 12 products plus the center column's
-// three couplings sum_t H_t(c, c) V_t(k, k + dk).  The column's 36 factors
-// stay in registers; per node the launch reads f, the 9 x values of the
-// layer two ahead (issued before the row's store) and writes one value.
+// group (pi, pj) per launch, one thread per column, the layers bottom-up
+// (UP) or top-down.  A row needs the new x of the layer behind the sweep,
+// the old x of the layer ahead (its own column) and the other groups' old x
+// (the neighbour sums), all staged.
 template <bool UP>
-__global__ void __launch_bounds__(256) k_gs_sep(Grid g, const float* __restrict__ H,
-                                                const float* __restrict__ V,
-                                                const float* __restrict__ f,
-                                                float* __restrict__ x, int pi, int pj) {
-  const int ih = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jh = blockIdx.y * blockDim.y + threadIdx.y;
-  const int i = 2 * ih + pi, j = 2 * jh + pj;
-  if (i < 1 || i > g.Nx - 2 || j < 1 || j > g.Ny - 2) return;
-  int off[9];
-  column_offsets(g, i, off);
-  const int64_t own = (int64_t)j * g.RP + (int64_t)(i & 1) * g.H + (i >> 1);
-  float hf[4][9];
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-#pragma unroll
-    for (int c = 0; c < 9; ++c) hf[t][c] = H[hidx(own, 9 * t + c)];
-  const int64_t PP = g.PP;
-  const int Nz = g.Nz;
-  float nb[9];
-  auto load = [&](int k) {
-    const float* xl = x + (int64_t)k * PP + own;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) nb[c] = xl[off[c]];
-  };
-  auto nsum = [&](float y[4]) {
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float s = 0.0f;
-#pragma unroll
-      for (int c = 0; c < 9; ++c)
-        if (c != 4) s = fmaf(hf[t][c], nb[c], s);
-      y[t] = s;
-    }
-  };
-  float Yn[4], Y0[4], Yf[4];  // neighbour sums: the layer behind, this one, the one ahead
-  float xn_behind = 0.0f, x_ahead = 0.0f;
-  const int kfirst = UP ? 0 : Nz - 2;
-  const int step = UP ? 1 : -1;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) Yn[t] = 0.0f;
-  if (UP) {
-    load(0);
-    nsum(Y0);
-    load(1);
-    nsum(Yf);
-    x_ahead = nb[4];
-  } else {
-    // the top layer is fixed: x = 0 there and its couplings are zero
-#pragma unroll
-    for (int t = 0; t < 4; ++t) Yn[t] = 0.0f;
-    load(kfirst);
-    nsum(Y0);
-    if (kfirst >= 1) {
-      load(kfirst - 1);
-      nsum(Yf);
-      x_ahead = nb[4];
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) Yf[t] = 0.0f;
-    }
-  }
-  // behind / ahead in V's offsets: UP reads dk = -1 behind, +1 ahead
-  const int vb = UP ? 0 : 2, va = UP ? 2 : 0;
-  for (int q = 0, k = kfirst; q <= Nz - 2; ++q, k += step) {
-    const int k2 = k + 2 * step;
-    const bool more = UP ? (k2 <= Nz - 1) : (k2 >= 0);
-    if (more) load(k2);
-    const float* v = V + k * kVF;
-    float acc = f[(int64_t)k * PP + own];
-    // the layer behind the sweep first, the layer ahead (loaded last) last
-#pragma unroll
-    for (int t = 0; t < 4; ++t) acc = fmaf(-v[3 * t + vb], Yn[t], acc);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) acc = fmaf(-v[3 * t + 1], Y0[t], acc);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) acc = fmaf(-v[3 * t + va], Yf[t], acc);
-    float kb = 0.0f, dg = 0.0f, ka = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      kb = fmaf(hf[t][4], v[3 * t + vb], kb);
-      dg = fmaf(hf[t][4], v[3 * t + 1], dg);
-      ka = fmaf(hf[t][4], v[3 * t + va], ka);
-    }
-    acc = fmaf(-kb, xn_behind, acc);
-    acc = fmaf(-ka, x_ahead, acc);
-    const float xn = acc / dg;
-    x[(int64_t)k * PP + own] = xn;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      Yn[t] = Y0[t];
-      Y0[t] = Yf[t];
-    }
-    xn_behind = xn;
-    if (more) {
-      nsum(Yf);
-      x_ahead = nb[4];
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) Yf[t] = 0.0f;
-      x_ahead = 0.0f;
-    }
-  }
-}
-
-// The same sweep with the x values staged through shared memory.  A block
-// owns kGsR rows x 32 same-group columns; for every free layer it needs the
-// x values of rows j0-1 .. j0+2kGsR-1, both parity halves, half-row indices
-// [h0-4, h0+36) (the 9 columns around each of its columns; 16-byte aligned
-// windows), and f of its own columns.  Warp 0 copies those with bulk
-// asynchronous copies (one per half-row segment) into a ring of kStages
-// shared-memory stages, kStages-1 layers ahead of the layer in use, each
-// stage's arrival counted in bytes on its mbarrier.  The threads read their
-// 9 neighbours from the stage, so a block keeps about 10 KB of loads in
-// flight with no registers held for them.  Only this group's columns are
-// written in the launch, and a thread needs the old x of other groups' columns
-// and of its own column above (below) the row it updates, so the staged
-// values are the ones the sweep must read.  A wait that runs out sets the
-// status bit and ends the block (after waiting, bounded, for its copies).
-constexpr int kGsR = 4;
-constexpr int kTileRows = 2 * kGsR + 1;
-constexpr int kTileW = 40;
-constexpr int kStageX = kTileRows * 2 * kTileW;
-constexpr int kStage = kStageX + kGsR * 32;
-constexpr int kStages = 8;
-
-template <bool UP>
-__global__ void __launch_bounds__(32 * kGsR) k_gs_sep_staged(Grid g, const float* __restrict__ H,
-                                                            const float* __restrict__ V,
-                                                            const float* __restrict__ f,
-                                                            float* __restrict__ x, int pi, int pj,
-                                                            int* status) {
-  __shared__ __align__(128) float tile[kStages][kStage];
-  __shared__ __align__(8) uint64_t bar[kStages];
+__global__ void __launch_bounds__(32 * (kGsR + 1)) k_gs_sep_staged(
+    Grid g, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmf,
+    const float* __restrict__ H, const float* __restrict__ V, float* __restrict__ x, int pi, int pj,
+    int* status) {
+  __shared__ __align__(128) float tile[kStages][kGsStage];
+  __shared__ __align__(16) float vsh[kMaxZ * kVF];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int h0 = blockIdx.x * 32;
   const int j0 = 2 * kGsR * blockIdx.y + pj;
-  const int h = h0 + tx, j = j0 + 2 * ty, i = 2 * h + pi;
-  const bool active = i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2;
   const int nlay = g.Nz - 1;  // free layers; the top layer is fixed (x = 0)
-  const int64_t PP = g.PP;
   if (ty == 0 && tx == 0) {
-    for (int q = 0; q < kStages; ++q) mbar_init(&bar[q], 1);
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kGsR);
+    }
     fence_barrier_init();
   }
+  for (int q = ty * 32 + tx; q < nlay * kVF; q += 32 * (kGsR + 1)) vsh[q] = V[q];
   __syncthreads();
-  // warp 0: the copies of free layer number t (sweep order) into stage t % kStages
-  auto issue = [&](int t) {
-    const int k = UP ? t : nlay - 1 - t;
-    float* st = tile[t % kStages];
-    const int q = tx;
-    const float* src = nullptr;
-    float* dst = nullptr;
-    uint32_t bytes = 0;
-    if (q < 2 * kTileRows) {
-      const int r = q >> 1, par = q & 1, jj = j0 - 1 + r;
-      const int lo = max(h0 - 4, 0), hi = min(h0 + 36, g.H);
-      if (jj >= 0 && jj < g.Ny) {
-        src = x + (int64_t)k * PP + (int64_t)jj * g.RP + (int64_t)par * g.H + lo;
-        dst = st + (r * 2 + par) * kTileW + (lo - (h0 - 4));
-        bytes = (uint32_t)(hi - lo) * 4u;
-      }
-    } else if (q < 2 * kTileRows + kGsR) {
-      const int r = q - 2 * kTileRows, jj = j0 + 2 * r;
-      if (jj < g.Ny) {
-        src = f + (int64_t)k * PP + (int64_t)jj * g.RP + (int64_t)pi * g.H + h0;
-        dst = st + kStageX + r * 32;
-        bytes = 128u;
-      }
-    }
-    const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
-    if (q == 0) mbar_arrive_expect_tx(&bar[t % kStages], total);
-    __syncwarp();
-    if (bytes) bulk_copy_g2s(dst, src, bytes, &bar[t % kStages]);
-  };
-  int issued = 0;
-  if (ty == 0) {
-    for (int t = 0; t < kStages - 1 && t < nlay; ++t) issue(t);
-    issued = min(kStages - 1, nlay);
+  if (ty == kGsR) {
+    produce<kGsStage>(tile, full, empty, nlay, UP, kGsBytes, kGsX, &tmx, &tmf, h0 - 4, j0 - 1,
+                      h0, pi, j0, status);
+    return;
   }
+  const int h = h0 + tx, j = j0 + 2 * ty, i = 2 * h + pi;
+  const bool active = i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2;
   const int64_t own = (int64_t)j * g.RP + (int64_t)pi * g.H + h;
-  float hf[4][9];
+  float hf[4][9];  // P, S, T, R
   int toff[9];
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
@@ -551,71 +489,70 @@ __global__ void __launch_bounds__(32 * kGsR) k_gs_sep_staged(Grid g, const float
   for (int t = 0; t < 4; ++t)
 #pragma unroll
     for (int c = 0; c < 9; ++c) hf[t][c] = active ? H[hidx(own, 9 * t + c)] : 0.0f;
+  // vertical offsets of the layer behind / ahead of the sweep
   const int vb = UP ? 0 : 2, va = UP ? 2 : 0;
-  float Yb[4], Yc[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) Yb[q] = Yc[q] = 0.0f;
+  const int ab = UP ? 6 : 7, aa = UP ? 7 : 6;
+  const int fo = kGsX + 2 * ty * 32 + tx;
+  float Pb = 0.0f, Sb = 0.0f, Rb = 0.0f, Pc = 0.0f, Sc = 0.0f, Rc = 0.0f;
+  float yT0 = 0.0f;  // T-sum of the ground layer (its only row with B != 0)
   float xb = 0.0f;
   for (int t = 0; t <= nlay; ++t) {
-    float Yt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float xt = 0.0f;
+    float Pt = 0.0f, St = 0.0f, Rt = 0.0f, xt = 0.0f;
     if (t < nlay) {
-      const bool ok = wait_parity(&bar[t % kStages], (uint32_t)(t / kStages) & 1u, status,
+      const bool ok = wait_parity(&full[t & (kStages - 1)], (uint32_t)(t / kStages) & 1u, status,
                                   kWaitLimitNs);
-      if (__syncthreads_or(!ok)) {
-        // bounded wait for the copies still in flight, then leave
-        if (ty == 0 && tx == 0)
-          for (int u = t + 1; u < issued; ++u)
-            wait_parity(&bar[u % kStages], (uint32_t)(u / kStages) & 1u, status, kWaitLimitNs);
-        return;
-      }
+      if (__any_sync(0xffffffffu, !ok)) return;  // the warp leaves together
       if (active) {
-        const float* st = tile[t % kStages];
+        const float* st = tile[t & (kStages - 1)];
+        float nb[9];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float sum = 0.0f;
+        for (int c = 0; c < 9; ++c) nb[c] = st[toff[c]];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          if (c == 4) continue;
+          Pt = fmaf(hf[0][c], nb[c], Pt);
+          St = fmaf(hf[1][c], nb[c], St);
+          Rt = fmaf(hf[3][c], nb[c], Rt);
+        }
+        if ((UP ? t : nlay - 1 - t) == 0) {
 #pragma unroll
           for (int c = 0; c < 9; ++c)
-            if (c != 4) sum = fmaf(hf[q][c], st[toff[c]], sum);
-          Yt[q] = sum;
+            if (c != 4) yT0 = fmaf(hf[2][c], nb[c], yT0);
         }
-        xt = st[toff[4]];
+        xt = nb[4];
       }
     }
-    if (t >= 1 && active) {
-      // row of free layer number t-1: behind = t-2, ahead = t
-      const int kr = UP ? t - 1 : nlay - t;
-      const float* v = V + kr * kVF;
-      float acc = tile[(t - 1) % kStages][kStageX + ty * 32 + tx];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc = fmaf(-v[3 * q + vb], Yb[q], acc);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc = fmaf(-v[3 * q + 1], Yc[q], acc);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc = fmaf(-v[3 * q + va], Yt[q], acc);
-      float kb = 0.0f, dg = 0.0f, ka = 0.0f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        kb = fmaf(hf[q][4], v[3 * q + vb], kb);
-        dg = fmaf(hf[q][4], v[3 * q + 1], dg);
-        ka = fmaf(hf[q][4], v[3 * q + va], ka);
+    if (t >= 1) {
+      if (active) {
+        // row of free layer number t-1: behind = t-2, ahead = t
+        const int kr = UP ? t - 1 : nlay - t;
+        const float4 v0 = *reinterpret_cast<const float4*>(vsh + kr * kVF);
+        const float4 v1 = *reinterpret_cast<const float4*>(vsh + kr * kVF + 4);
+        const float v[9] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, vsh[kr * kVF + 8]};
+        float acc = tile[(t - 1) & (kStages - 1)][fo];
+        acc = fmaf(-v[vb], Pb, acc);
+        acc = fmaf(-v[3 + vb], Rb, acc);
+        acc = fmaf(-v[ab], Sb, acc);
+        acc = fmaf(-v[1], Pc, acc);
+        acc = fmaf(-v[4], Rc, acc);
+        acc = fmaf(-v[8], yT0, acc);
+        acc = fmaf(-v[va], Pt, acc);
+        acc = fmaf(-v[3 + va], Rt, acc);
+        acc = fmaf(-v[aa], St, acc);
+        const float kb = fmaf(hf[0][4], v[vb], hf[3][4] * v[3 + vb]);
+        const float ka = fmaf(hf[0][4], v[va], hf[3][4] * v[3 + va]);
+        const float dg = fmaf(hf[0][4], v[1], fmaf(hf[3][4], v[4], hf[2][4] * v[8]));
+        acc = fmaf(-ka, xt, acc);
+        acc = fmaf(-kb, xb, acc);
+        xb = __fdividef(acc, dg);
+        x[(int64_t)kr * g.PP + own] = xb;
       }
-      acc = fmaf(-kb, xb, acc);
-      acc = fmaf(-ka, xt, acc);
-      xb = acc / dg;
-      x[(int64_t)kr * PP + own] = xb;
+      // this warp no longer reads the stage of layer t-1
+      __syncwarp();
+      if (tx == 0) mbar_arrive(&empty[(t - 1) & (kStages - 1)]);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      Yb[q] = Yc[q];
-      Yc[q] = Yt[q];
-    }
-    __syncthreads();  // stage (t - 1) % kStages is free
-    if (ty == 0 && issued < nlay && issued == t + kStages - 1) {
-      fence_proxy_async_shared();
-      issue(issued);
-      ++issued;
-    }
+    Pb = Pc; Sb = Sc; Rb = Rc;
+    Pc = Pt; Sc = St; Rc = Rt;
   }
 }
 
@@ -639,126 +576,141 @@ __global__ void __launch_bounds__(128) k_gs_sep_zero_start(Grid g, const float* 
     for (int k = 0; k < g.Nz; ++k) x[(int64_t)k * PP + own] = 0.0f;
     return;
   }
-  float hc[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) hc[t] = H[hidx(own, 9 * t + 4)];
+  const float Pc = H[hidx(own, 4)], Tc = H[hidx(own, 22)], Rc = H[hidx(own, 31)];
   float prev = 0.0f;
   for (int k = 0; k <= g.Nz - 2; ++k) {
     const float* v = V + k * kVF;
-    float kb = 0.0f, dg = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      kb = fmaf(hc[t], v[3 * t], kb);
-      dg = fmaf(hc[t], v[3 * t + 1], dg);
-    }
-    const float acc = fmaf(-kb, prev, f[(int64_t)k * PP + own]);
-    prev = acc / dg;
+    const float kb = fmaf(Pc, v[0], Rc * v[3]);
+    const float dg = fmaf(Pc, v[1], fmaf(Rc, v[4], Tc * v[8]));
+    prev = __fdividef(fmaf(-kb, prev, f[(int64_t)k * PP + own]), dg);
     x[(int64_t)k * PP + own] = prev;
   }
   x[(int64_t)(g.Nz - 1) * PP + own] = 0.0f;
 }
 
-// r = f - K x on the separable float32 operator, one thread per column
-// (blockIdx.z = parity of i), with the full 9-column sums
-// y_t(k') = sum_d H_t(c, c + d) x(c + d, k') formed once per layer.
-// FUSE = false: writes r (0 at fixed nodes).  FUSE = true, for a transfer
-// that keeps the columns (vertical coarsening only): restricts on the fly,
-// f_c(K) = sum_k P(k, K) r(k) (Eq. 7 first row) with the layer weights of
-// the transfer, so r is never stored; fc is on the coarse grid (same
-// columns, tr.Nzc layers).
+// r = f - K x on the separable float32 operator, one thread per column of
+// one parity half (blockIdx.z), owned rows j0 .. j0+kGsR-1, with the full
+// 9-column sums formed once per layer.  FUSE = false: writes r (0 at fixed
+// nodes and padding).  FUSE = true, for a transfer that keeps the columns
+// (vertical coarsening only): restricts on the fly, f_c(K) = sum_k P(k, K)
+// r(k) (Eq. 7 first row) with the layer weights of the transfer, so r is
+// never stored; out is then the coarse f (same columns, tr.Nzc layers).
 template <bool FUSE>
-__global__ void __launch_bounds__(128) k_residual_sep(Grid g, Transfer tr,
-                                                      const float* __restrict__ H,
-                                                      const float* __restrict__ V,
-                                                      const float* __restrict__ f,
-                                                      const float* __restrict__ x,
-                                                      float* __restrict__ out) {
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(32 * (kGsR + 1)) k_residual_sep_staged(
+    Grid g, const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmf,
+    const __grid_constant__ Transfer tr, const float* __restrict__ H, const float* __restrict__ V,
+    float* __restrict__ out, int* status) {
+  __shared__ __align__(128) float tile[kStages][kResStage];
+  __shared__ __align__(16) float vsh[kMaxZ * kVF];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  const int tx = threadIdx.x, ty = threadIdx.y;
   const int par = (int)blockIdx.z;
-  if (h >= g.H || j >= g.Ny) return;
-  const int i = 2 * h + par;
-  const int64_t own = (int64_t)j * g.RP + (int64_t)par * g.H + h;
+  const int h0 = blockIdx.x * 32;
+  const int j0 = kGsR * blockIdx.y;
+  const int nlay = g.Nz - 1;
   const int64_t PP = g.PP;
-  const int Nz = g.Nz;
-  const int Nout = FUSE ? tr.Nzc : Nz;
-  if (!(i < g.Nx && free_column(g, i, j))) {
-    for (int k = 0; k < Nout; ++k) out[(int64_t)k * PP + own] = 0.0f;
+  if (ty == 0 && tx == 0) {
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kGsR);
+    }
+    fence_barrier_init();
+  }
+  for (int q = ty * 32 + tx; q < nlay * kVF; q += 32 * (kGsR + 1)) vsh[q] = V[q];
+  __syncthreads();
+  if (ty == kGsR) {
+    produce<kResStage>(tile, full, empty, nlay, true, kResBytes, kResX, &tmx, &tmf, h0 - 4,
+                       j0 - 1, h0, par, j0, status);
     return;
   }
-  int off[9];
-  column_offsets(g, i, off);
+  const int h = h0 + tx, j = j0 + ty, i = 2 * h + par;
+  const bool inrow = j < g.Ny;
+  const bool active = inrow && i < g.Nx && free_column(g, i, j);
+  const int64_t own = (int64_t)j * g.RP + (int64_t)par * g.H + h;
   float hf[4][9];
+  int toff[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const int ii = i + c % 3 - 1, r = ty + 1 + c / 3 - 1;
+    toff[c] = (r * 2 + (ii & 1)) * kTileW + ((ii >> 1) - (h0 - 4));
+  }
 #pragma unroll
   for (int t = 0; t < 4; ++t)
 #pragma unroll
-    for (int c = 0; c < 9; ++c) hf[t][c] = H[hidx(own, 9 * t + c)];
-  float nb[9];
-  auto load = [&](int k) {
-    const float* xl = x + (int64_t)k * PP + own;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) nb[c] = xl[off[c]];
-  };
-  auto fsum = [&](float y[4]) {
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float s = 0.0f;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) s = fmaf(hf[t][c], nb[c], s);
-      y[t] = s;
-    }
-  };
-  float Yb[4], Y0[4], Y1[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) Yb[t] = 0.0f;
-  load(0);
-  fsum(Y0);
-  load(1);
-  fsum(Y1);
+    for (int c = 0; c < 9; ++c) hf[t][c] = active ? H[hidx(own, 9 * t + c)] : 0.0f;
+  const int fo = kResX + ty * 32 + tx;
+  float Pb = 0.0f, Sb = 0.0f, Rb = 0.0f, Pc = 0.0f, Sc = 0.0f, Rc = 0.0f;
+  float T0 = 0.0f;
   int Kcur = 0;
   float accLo = 0.0f, accHi = 0.0f;
-  for (int k = 0; k <= Nz - 2; ++k) {
-    const bool more = k + 2 <= Nz - 1;
-    if (more) load(k + 2);
-    const float* v = V + k * kVF;
-    float r = f[(int64_t)k * PP + own];
+  for (int t = 0; t <= nlay; ++t) {
+    float Pt = 0.0f, St = 0.0f, Rt = 0.0f;
+    if (t < nlay) {
+      const bool ok = wait_parity(&full[t & (kStages - 1)], (uint32_t)(t / kStages) & 1u, status,
+                                  kWaitLimitNs);
+      if (__any_sync(0xffffffffu, !ok)) return;
+      if (active) {
+        const float* st = tile[t & (kStages - 1)];
+        float nb[9];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) r = fmaf(-v[3 * t], Yb[t], r);
+        for (int c = 0; c < 9; ++c) nb[c] = st[toff[c]];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) r = fmaf(-v[3 * t + 1], Y0[t], r);
+        for (int c = 0; c < 9; ++c) {
+          Pt = fmaf(hf[0][c], nb[c], Pt);
+          if (c != 4) St = fmaf(hf[1][c], nb[c], St);
+          Rt = fmaf(hf[3][c], nb[c], Rt);
+        }
+        if (t == 0) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) r = fmaf(-v[3 * t + 2], Y1[t], r);
-    if (FUSE) {
-      const int c0 = tr.kc0[k], c1 = tr.kc1[k];
-      if (c0 > Kcur) {  // coarse layer Kcur has all its fine contributions
-        out[(int64_t)Kcur * PP + own] = accLo;
-        accLo = accHi;
-        accHi = 0.0f;
-        Kcur = c0;
+          for (int c = 0; c < 9; ++c) T0 = fmaf(hf[2][c], nb[c], T0);
+        }
       }
-      accLo = fmaf(tr.kw0[k], r, accLo);
-      if (c1 != c0) accHi = fmaf(tr.kw1[k], r, accHi);
-    } else {
-      out[(int64_t)k * PP + own] = r;
     }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      Yb[t] = Y0[t];
-      Y0[t] = Y1[t];
+    if (t >= 1) {
+      const int k = t - 1;
+      float r = 0.0f;
+      if (active) {
+        const float4 v0 = *reinterpret_cast<const float4*>(vsh + k * kVF);
+        const float4 v1 = *reinterpret_cast<const float4*>(vsh + k * kVF + 4);
+        r = tile[k & (kStages - 1)][fo];
+        r = fmaf(-v0.x, Pb, r);
+        r = fmaf(-v0.w, Rb, r);
+        r = fmaf(-v1.z, Sb, r);
+        r = fmaf(-v0.y, Pc, r);
+        r = fmaf(-v1.x, Rc, r);
+        r = fmaf(-vsh[k * kVF + 8], T0, r);
+        r = fmaf(-v0.z, Pt, r);
+        r = fmaf(-v1.y, Rt, r);
+        r = fmaf(-v1.w, St, r);
+      }
+      __syncwarp();
+      if (tx == 0) mbar_arrive(&empty[k & (kStages - 1)]);
+      if (inrow) {
+        if (FUSE) {
+          const int c0 = tr.kc0[k], c1 = tr.kc1[k];
+          if (c0 > Kcur) {  // coarse layer Kcur has all its fine contributions
+            out[(int64_t)Kcur * PP + own] = accLo;
+            accLo = accHi;
+            accHi = 0.0f;
+            Kcur = c0;
+          }
+          accLo = fmaf(tr.kw0[k], r, accLo);
+          if (c1 != c0) accHi = fmaf(tr.kw1[k], r, accHi);
+        } else {
+          out[(int64_t)k * PP + own] = r;
+        }
+      }
     }
-    if (more) {
-      fsum(Y1);
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) Y1[t] = 0.0f;
-    }
+    Pb = Pc; Sb = Sc; Rb = Rc;
+    Pc = Pt; Sc = St; Rc = Rt;
   }
+  if (!inrow) return;
   if (FUSE) {
     // the last fine free layer ends coarse layer Nzc - 2; the top is fixed
     out[(int64_t)Kcur * PP + own] = accLo;
-    for (int K = Kcur + 1; K < Nout; ++K) out[(int64_t)K * PP + own] = 0.0f;
+    for (int K = Kcur + 1; K < tr.Nzc; ++K) out[(int64_t)K * PP + own] = 0.0f;
   } else {
-    out[(int64_t)(Nz - 1) * PP + own] = 0.0f;
+    out[(int64_t)(g.Nz - 1) * PP + own] = 0.0f;
   }
 }
 
@@ -803,8 +755,8 @@ cudaError_t launch_hgalerkin(int dim, const Grid& gin, const Grid& gout, const d
 }
 
 cudaError_t launch_vfactor0(int Nx, int Ny, int Nz, const double* Z, double* V64, float* V32,
-                            cudaStream_t st) {
-  k_vfactor0<<<1, 32, 0, st>>>(Nx, Ny, Nz, Z, V64, V32);
+                            int* flag, cudaStream_t st) {
+  k_vfactor0<<<1, 32, 0, st>>>(Nx, Ny, Nz, Z, V64, V32, flag);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -837,48 +789,70 @@ template cudaError_t launch_sep_export<double>(const Grid&, const double*, const
 template cudaError_t launch_sep_export<float>(const Grid&, const float*, const float*, double*,
                                               cudaStream_t);
 
-cudaError_t launch_gs_sep(const Grid& g, const float* H32, const float* V32, const float* f,
-                          float* x, int group, int up, int rows, cudaStream_t st) {
+cudaError_t launch_gs_sep_staged(const Level& L, const float* H32, const float* V32, float* x,
+                                 int group, int up, int* status, cudaStream_t st) {
+  const Grid& g = L.g;
   const int pi = group & 1, pj = group >> 1;
-  const dim3 blk(32, rows);
-  const dim3 grd(((g.Nx + 1) / 2 + 31) / 32, ((g.Ny + 1) / 2 + rows - 1) / rows);
-  if (up) k_gs_sep<true><<<grd, blk, 0, st>>>(g, H32, V32, f, x, pi, pj);
-  else k_gs_sep<false><<<grd, blk, 0, st>>>(g, H32, V32, f, x, pi, pj);
+  const dim3 blk(32, kGsR + 1);
+  const dim3 grd(((g.Nx + 1) / 2 + 31) / 32, ((g.Ny + 1) / 2 + kGsR - 1) / kGsR);
+  if (up) k_gs_sep_staged<true><<<grd, blk, 0, st>>>(g, L.tm_x, L.tm_f, H32, V32, x, pi, pj, status);
+  else k_gs_sep_staged<false><<<grd, blk, 0, st>>>(g, L.tm_x, L.tm_f, H32, V32, x, pi, pj, status);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gs_sep_staged(const Grid& g, const float* H32, const float* V32,
-                                 const float* f, float* x, int group, int up, int* status,
-                                 cudaStream_t st) {
-  const int pi = group & 1, pj = group >> 1;
-  const dim3 blk(32, kGsR);
-  const dim3 grd(((g.Nx + 1) / 2 + 31) / 32, ((g.Ny + 1) / 2 + kGsR - 1) / kGsR);
-  if (up) k_gs_sep_staged<true><<<grd, blk, 0, st>>>(g, H32, V32, f, x, pi, pj, status);
-  else k_gs_sep_staged<false><<<grd, blk, 0, st>>>(g, H32, V32, f, x, pi, pj, status);
+cudaError_t launch_residual_sep_staged(const Level& L, bool fuse, const float* H32,
+                                       const float* V32, float* out, int* status,
+                                       cudaStream_t st) {
+  const Grid& g = L.g;
+  const dim3 blk(32, kGsR + 1);
+  const dim3 grd((g.H + 31) / 32, (g.Ny + kGsR - 1) / kGsR, 2);
+  if (fuse)
+    k_residual_sep_staged<true><<<grd, blk, 0, st>>>(g, L.tm_rx, L.tm_rf, L.tr, H32, V32, out, status);
+  else
+    k_residual_sep_staged<false><<<grd, blk, 0, st>>>(g, L.tm_rx, L.tm_rf, L.tr, H32, V32, out, status);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// Tensor maps of a level's float32 x and f for the staged kernels: each
+// array as a 4-D tensor [Nz][Ny][2][H] (half-row index innermost, then the
+// parity half, the row and the layer); boxes of 40 x 2 x 9 (smoother) or
+// 40 x 2 x 6 (residual) x values and 32 x 1 x 7 or 32 x 1 x 4 f values,
+// zero fill outside.
+cudaError_t make_tile_maps(Level& L, float* x32, float* f32) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode,
+                                                     12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !encode) return cudaErrorNotSupported;
+  }
+  const Grid& g = L.g;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.H, 2, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.H * 4, (cuuint64_t)g.RP * 4, (cuuint64_t)g.PP * 4};
+  const cuuint32_t ones[4] = {1, 1, 1, 1};
+  struct Map { CUtensorMap* m; float* base; cuuint32_t box[4]; };
+  const Map maps[4] = {
+      {&L.tm_x, x32, {(cuuint32_t)kTileW, 2, (cuuint32_t)kGsTileRows, 1}},
+      {&L.tm_f, f32, {32, 1, (cuuint32_t)kGsFRows, 1}},
+      {&L.tm_rx, x32, {(cuuint32_t)kTileW, 2, (cuuint32_t)kResTileRows, 1}},
+      {&L.tm_rf, f32, {32, 1, (cuuint32_t)kGsR, 1}}};
+  for (const Map& mp : maps) {
+    const CUresult r = encode(mp.m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, mp.base, dims, strides,
+                              mp.box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_gs_sep_zero_start(const Grid& g, const float* H32, const float* V32,
                                      const float* f, float* x, int group, cudaStream_t st) {
   const dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
   k_gs_sep_zero_start<<<grd, dim3(32, 4), 0, st>>>(g, H32, V32, f, x, group & 1, group >> 1);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_residual_sep(const Grid& g, const Transfer* fuse, const float* H32,
-                                const float* V32, const float* f, const float* x, float* out,
-                                cudaStream_t st) {
-  const dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2), blk(32, 4);
-  if (fuse) {
-    k_residual_sep<true><<<grd, blk, 0, st>>>(g, *fuse, H32, V32, f, x, out);
-  } else {
-    Transfer none;
-    none.Nzc = g.Nz;
-    k_residual_sep<false><<<grd, blk, 0, st>>>(g, none, H32, V32, f, x, out);
-  }
   count_launches(1);
   return cudaGetLastError();
 }
