@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mcwind", choices=["mcwind", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
-    ap.add_argument("--op-form", default="stored", choices=["stored", "separable"],
+    ap.add_argument("--op-form", default="separable", choices=["stored", "separable"],
                     help="float32 cycle on stored 27-point rows or on the column x layer "
                          "factors of the shift-form grid (mixed precision)")
     ap.add_argument("--cells", type=int, nargs=3, default=list(CELLS))
@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-f64-compare", action="store_true")
     ap.add_argument("--workload", default="domain", choices=["domain", "batched", "rates"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 96-domain batched workload in the default run")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--launch-summary", default=None, metavar="CSV",
                     help="print per-kernel launches, time and share from an ncu "
@@ -115,19 +117,53 @@ def run_cpu_sample(steps=1, warmup=0):
             "steps": steps, "n_free": c.n_free}
 
 
-def cpu_baseline_subprocess():
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def cpu_sample_subprocess(threads):
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "1"],
                          env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         return {"error": out.stderr[-400:]}
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (plain C + scipy, one thread) on cells [{SAMPLE_I0},{SAMPLE_I0 + SAMPLE_W})^2 x 15 "
-                       f"of the same domain ({r['n_free']} free unknowns): assembly + hierarchy, "
-                       f"cold + warm V-cycle solves to 1e-8, recovery; {r['cycles']} V-cycles in "
-                       f"{r['seconds']:.1f} s"),
-            "seconds": r["seconds"]}
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_subprocess():
+    """The oracle on the bounded window with all host threads (its OpenMP
+    element loops; the multigrid's sparse products run in one thread), and
+    again with one thread."""
+    ncpu = os.cpu_count() or 1
+    many = cpu_sample_subprocess(ncpu)
+    one = cpu_sample_subprocess(1)
+    if "error" in many:
+        return many
+    sample = (f"oracle (plain C with OpenMP + scipy) on cells [{SAMPLE_I0},{SAMPLE_I0 + SAMPLE_W})^2 x 15 "
+              f"of the same domain ({many['n_free']} free unknowns): assembly + hierarchy, "
+              f"cold + warm V-cycle solves to 1e-8, recovery; {many['cycles']} V-cycles in "
+              f"{many['seconds']:.1f} s")
+    return {"value": many["value"], "unit": UNIT, "cores": ncpu, "nproc": ncpu, "kind": "oracle",
+            "sample": sample, "seconds": many["seconds"],
+            "one_thread": ({"value": one["value"], "seconds": one["seconds"], "cores": 1}
+                           if "error" not in one else one)}
+
+
+def oracle_full_size(case, lam_h, u0):
+    """The oracle at full size (its OpenMP element loops, all host threads):
+    the load vector of Eq. 5 and the residual certificate
+    ||f - K lambda_gpu|| / ||f||, each timed."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    f = oracle.assemble_f(case, u0=u0, parallel=True)
+    t1 = time.perf_counter()
+    r = f - oracle.apply_K(case, lam_h)
+    t2 = time.perf_counter()
+    free = oracle.case_free_mask(case)
+    cert = float(np.linalg.norm(r[free]) / np.linalg.norm(f[free]))
+    return {"kind": "oracle", "cores": os.cpu_count() or 1, "load_vector_s": t1 - t0,
+            "residual_certificate_s": t2 - t1, "certificate_rel_res": cert,
+            "sample": "full 3000x3000x15 domain: oracle load vector and ||f - K lambda||/||f|| "
+                      "of the GPU's cold-solve lambda, both element by element in float64"}
 
 
 def run_reference(args):
@@ -314,11 +350,14 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse):
     return {k: v for k, v in U.items() if v}
 
 
-def bench_batched(args):
+def run_batched(steps, warmup, autotune_on=True):
     """96 independent domains (horizontal cells uniform in [48, 384] per axis,
-    8-20 layers, a3 in {1, 4, 10}), mixed precision, per-domain autotuned
-    sweeps and smoother block shape, solved together to 1e-8 (one CUDA graph
-    per iteration with a branch per domain)."""
+    8-20 layers, a3 in {1, 4, 10}), mixed precision with the separable
+    operator, per-domain autotuned sweeps, solved together to 1e-8 by one CUDA
+    graph launch per solve (a conditional loop with an IF node per domain).
+    Every domain of the timed solve is certified by the oracle
+    (||f - K lambda|| / ||f||, element by element in float64); the 4
+    smallest are also compared element-wise with the oracle's own solve."""
     import numpy as np
     import torch
 
@@ -333,70 +372,84 @@ def bench_batched(args):
     plans, u0s = [], []
     for c in cases:
         X, Y, Z, u0 = (torch.from_numpy(a).cuda() for a in (c.X, c.Y, c.Z, c.u0))
-        p = m.Plan.for_case(c, precision=m.PREC_MIXED)
+        p = m.Plan.for_case(c, precision=m.PREC_MIXED, op_form=m.OP_SEPARABLE)
         p.assemble(X, Y, Z)
         p._keep = (X, Y, Z)
         plans.append(p)
         u0s.append(u0)
     n_free = [c.n_free for c in cases]
     t0 = time.perf_counter()
-    tuned = None
-    if not args.no_autotune:
-        tuned = autotune.tune_batch(plans, u0s, rtol=RTOL)
+    tuned = autotune.tune_batch(plans, u0s, rtol=RTOL) if autotune_on else None
     t_tune = time.perf_counter() - t0
     batch = m.Batch(plans)
     lams = [torch.zeros(p.node_shape, dtype=torch.float64, device="cuda") for p in plans]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.solve(u0s, lams, rtol=RTOL)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    iters = 0
     dom_cycles = 0
-    for _ in range(args.steps):
+    stats = None
+    for _ in range(steps):
         for l in lams:
             l.zero_()
         _, stats = batch.solve(u0s, lams, rtol=RTOL)
-        iters += max(st.cycles for st in stats)
         dom_cycles += sum(nf * st.cycles for nf, st in zip(n_free, stats))
     e1.record()
     torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    # the oracle's certificate of every domain's timed solution
+    certs = []
+    for c, lam, st in zip(cases, lams, stats):
+        lh = lam.cpu().numpy().ravel()
+        f = oracle.assemble_f(c, parallel=True)
+        free = oracle.case_free_mask(c)
+        r = f - oracle.apply_K(c, lh)
+        certs.append(float(np.linalg.norm(r[free]) / np.linalg.norm(f[free])))
     # the same domains one after another
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record()
-    seq_cycles = 0
     for p, u0, l in zip(plans, u0s, lams):
         l.zero_()
-        _, st = m.mcwind_solve(p.handle, u0, l, RTOL, 150, 0)
-        seq_cycles += st.cycles
+        m.mcwind_solve(p.handle, u0, l, RTOL, 150, 0)
     s1.record()
     torch.cuda.synchronize()
     t_seq = s0.elapsed_time(s1) / 1e3
-    # per-domain error against the oracle on the 4 smallest domains
-    lams, stats = batch.solve(u0s, lams, rtol=1e-11, max_cycles=250)
+    # element-wise against the oracle's own solve on the 4 smallest domains
+    lams2, _ = batch.solve(u0s, [torch.zeros_like(l) for l in lams], rtol=1e-11, max_cycles=250)
     small = sorted(range(len(cases)), key=lambda d: n_free[d])[:4]
-    errs = {cases[d].name: float(np.linalg.norm(lams[d].cpu().numpy().ravel() - (ref := oracle.solve(cases[d])))
-                                 / np.linalg.norm(ref)) for d in small}
-    cyc = max(st.cycles for st in stats)
+    errs = {}
+    for d in small:
+        ref = oracle.solve(cases[d])
+        errs[cases[d].name] = float(np.linalg.norm(lams2[d].cpu().numpy().ravel() - ref)
+                                    / np.linalg.norm(ref))
+    return {
+        "workload": "96 independent domains, horizontal cells U[48,384] per axis, 8-20 layers, "
+                    "a3 in {1,4,10}, random hills + log-law wind, mixed precision, separable "
+                    "operator, one graph launch per batch solve",
+        "n_free_total": sum(n_free), "rtol": RTOL,
+        "unknowns_per_s": sum(n_free) / t, "unknown_vcycles_per_s": dom_cycles / steps / t,
+        "batched_s": t, "sequential_s": t_seq, "batched_speedup": t_seq / t,
+        "graph_launches_per_solve": 1, "max_domain_cycles": max(st.cycles for st in stats),
+        "all_converged": all(st.status == 0 for st in stats),
+        "oracle_certificate_max": max(certs), "oracle_certificate_domains": len(certs),
+        "max_rel_err_vs_oracle_solve_smallest4": max(errs.values()),
+        "autotune_s": t_tune,
+        "tuning_sweeps": sorted({b[0] for b in tuned}) if tuned else None,
+    }
+
+
+def bench_batched(args):
+    """The batched workload alone (--workload batched)."""
+    r = run_batched(args.steps, args.warmup, autotune_on=not args.no_autotune)
     line = {
         "metric": "aggregate unknowns/s, 96 batched domains to 1e-8", "unit": "unknowns/s",
-        "value": sum(n_free) / t, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "96 independent domains, horizontal cells U[48,384] per axis, "
-                               "8-20 layers, a3 in {1,4,10}, random hills + log-law wind, "
-                               "mixed precision, one graph per iteration", "n_free_total": sum(n_free),
-                   "rtol": RTOL},
-        "unknown_vcycles_per_s": dom_cycles / args.steps / t,
-        "batch_iterations": iters // args.steps,
-        "sequential_s": t_seq, "batched_s": t, "batched_speedup": t_seq / t,
-        "autotune_s": t_tune,
-        "tuning": {c.name: list(b) for c, b in zip(cases, tuned)} if tuned else None,
-        "per_domain_max_rel_err_vs_oracle_smallest4": errs,
-        "domain_cycles_to_1e-8": [st.cycles for st in stats] if False else None,
+        "value": r["unknowns_per_s"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * r["batched_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": r["workload"], "n_free_total": r["n_free_total"], "rtol": RTOL},
+        "batched": r,
     }
-    line.pop("domain_cycles_to_1e-8")
     print(json.dumps(line), flush=True)
     return 0
 
@@ -641,14 +694,18 @@ def main():
 
     lam.zero_()
     t_cold, st_cold = time_solve(plan, U0, False)
+    lam_cold_h = lam.cpu().numpy().ravel() if (rank == 0 and not args.no_cpu_baseline) else None
     t_warm, st_warm = time_solve(plan, U0N, True)
     tt = {args.precision: {"cold_s": t_cold, "cold_cycles": st_cold.cycles,
                            "warm_s": t_warm, "warm_cycles": st_warm.cycles,
-                           "cold_rate": st_cold.rate}}
+                           "cold_rate": st_cold.rate,
+                           "form": ("float32 V-cycles (%s operator) inside float64 refinement; "
+                                    "element arithmetic in float pairs" % args.op_form)
+                           if prec == m.PREC_MIXED else "float64"}}
     prof_main = prof
     prof_f64 = None
     if not args.no_f64_compare and prec == m.PREC_MIXED:
-        del plan
+        plan = None
         torch.cuda.empty_cache()
         # the same solves accelerated by conjugate gradients (one V-cycle per iteration)
         pcg = m.Plan.for_case(case, precision=m.PREC_MIXED, accel=m.ACCEL_CG, op_form=op_form)
@@ -662,7 +719,8 @@ def main():
                           "warm_cycles": scw.cycles, "cold_rate": scc.rate}
         del pcg
         torch.cuda.empty_cache()
-        p64 = m.Plan.for_case(case, precision=m.PREC_F64)
+        # the plain float64 form: float64 element arithmetic too
+        p64 = m.Plan.for_case(case, precision=m.PREC_F64, element_arith=m.ARITH_F64)
         p64.assemble(X, Y, Z)
         lam.zero_()
         time_solve(p64, U0, False)
@@ -675,7 +733,9 @@ def main():
         f64_levels = [p64.level(l) for l in range(p64.num_levels)]
         f64_solves = [s64c.cycles, s64w.cycles]
         tt["f64"] = {"cold_s": t64c, "cold_cycles": s64c.cycles, "warm_s": t64w,
-                     "warm_cycles": s64w.cycles, "cold_rate": s64c.rate}
+                     "warm_cycles": s64w.cycles, "cold_rate": s64c.rate,
+                     "form": "plain float64: element arithmetic, stored operators and solve all "
+                             "in float64 (element_arith = ARITH_F64)"}
         del p64
 
     # ---- roofline of the dominant kernel class ---------------------------
@@ -748,9 +808,18 @@ def main():
         "fp64": "measured: FP64 FMA issue rate of this GB300, 5.81e11/s",
         "alu": "FP32 pipe: 128 lanes x 152 SMs x 2.07 GHz"}.get(dom_roof.get("bound"))
 
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        plan = None
+        del X, Y, Z, U0, U0N
+        torch.cuda.empty_cache()
+        batched = run_batched(steps=2, warmup=1, autotune_on=not args.no_autotune)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_subprocess()
+        if lam_cold_h is not None:
+            cpu["full_size"] = oracle_full_size(case, lam_cold_h, case.u0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -787,6 +856,7 @@ def main():
                                   if v[1]} if prof_f64 else None),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "batched_96_domains": batched,
         "clocks": clk,
         "input_gen_s": t_gen,
     }

@@ -332,28 +332,36 @@ int mcwind_residual_norm_noalloc(mcwind_plan plan, const double* f, const double
 
 /* ---- many independent domains ---------------------------------------------
  * A batch groups n assembled plans (independent domains of any sizes) whose
- * solves run together: each iteration of all domains is one CUDA graph with
- * one branch per domain, so the GPU overlaps the domains' kernels, and one
- * device-to-host copy returns every domain's residual.  Plans must use the
- * plain multigrid iteration (accel = MCWIND_ACCEL_NONE), stay assembled and
- * keep their workspaces while the batch lives; a plan belongs to at most
- * one batch.  Host arrays of device pointers are passed per domain. */
+ * solves run together.  One solve is ONE CUDA graph launch and one
+ * device-to-host read: per-domain set-up branches, then a conditional WHILE
+ * node whose body holds a conditional IF node per domain (its
+ * cycles_per_check V-cycles, refinement update and float64 residual) and a
+ * bookkeeping kernel that computes every domain's relative residual on the
+ * device, keeps iterating exactly the domains still above rtol and ends the
+ * loop when none is, or when the next check would pass max_cycles (so each
+ * domain gets exactly the result of its own mcwind_solve).  The graph is
+ * built on the first solve and rebuilt when the arguments (tolerance, cycle
+ * limit, flags, buffers) or a plan's workspace or tuning change.  Plans must
+ * use the plain multigrid iteration (accel = MCWIND_ACCEL_NONE), stay
+ * assembled and keep their workspaces while the batch lives; a plan belongs
+ * to at most one batch.  Host arrays of device pointers are passed per
+ * domain. */
 typedef struct mcwind_batch_s* mcwind_batch;
 
-/* Device workspace bytes a batch of n domains needs (n doubles, rounded up). */
+/* Device workspace bytes a batch of n domains needs (the per-domain
+ * residual histories and the graph's bookkeeping; about 2.1 KB per domain). */
 size_t mcwind_batch_workspace_bytes(int n);
 
 /* plans: host array of n assembled plans.  workspace: device, >=
  * mcwind_batch_workspace_bytes(n), 256-byte aligned, caller-owned. */
 int mcwind_batch_create(int n, const mcwind_plan* plans, void* workspace, mcwind_batch* out);
 
-/* Solve every domain d: u0[d], lambda[d] as in mcwind_solve.  Iterates until
- * every domain is at or below rtol or max_cycles; a domain stops iterating
- * once it reaches rtol (one cached graph per set of still-active domains), so
- * each domain gets exactly the result of its own mcwind_solve (checks every
- * cycles_per_check cycles of the first plan; give the plans one setting).  stats: host,
- * n entries, may be NULL.  Returns OK, ENOTCONV (some domain above rtol),
- * ENONFINITE, EINVAL. */
+/* Solve every domain d: u0[d], lambda[d] as in mcwind_solve.  Checks every
+ * cycles_per_check cycles of the first plan (give the plans one setting), up
+ * to the last check within max_cycles.  stats: host, n entries, may be NULL.
+ * Returns OK, ENOTCONV (some domain above rtol), ENONFINITE (some domain's
+ * wind is not finite; the others are solved), ETIMEOUT (a kernel's bounded
+ * wait ran out), EINVAL. */
 int mcwind_batch_solve(mcwind_batch batch, const double* const* u0, double* const* lambda,
                        double rtol, int max_cycles, unsigned flags, mcwind_stats* stats,
                        void* stream);
@@ -361,9 +369,19 @@ int mcwind_batch_solve(mcwind_batch batch, const double* const* u0, double* cons
 void mcwind_batch_destroy(mcwind_batch batch);
 
 /* Change the smoothing sweeps and the smoother's thread-block height (column
- * rows per block: 1, 2, 4 or 8; default 4) of an existing plan.  Used by the
- * batch autotuner; invalidates the plan's captured iteration graph. */
+ * rows per block: 1, 2, 4 or 8; default 4; the separable form's staged
+ * smoother always uses 4) of an existing plan.  Used by the batch autotuner;
+ * invalidates the plan's captured iteration graph. */
 int mcwind_plan_set_tuning(mcwind_plan plan, int nu_pre, int nu_post, int gs_block_rows);
+
+/* Self-test of the bounded device waits: one block waits, with the same
+ * bounded wait as the solver's kernels, on a barrier that nothing completes.
+ * The wait gives up after limit_us microseconds (1 .. 1e6), sets the plan's
+ * status word and the kernel returns; the call then returns MCWIND_ETIMEOUT,
+ * as a solve on this plan does until it is assembled again.  The GPU context
+ * stays usable throughout.  Synchronizes the stream.  The paper has no
+ * counterpart: this tests how the library reports a copy that never arrives. */
+int mcwind_plan_wait_selftest(mcwind_plan plan, int limit_us, void* stream);
 
 /* ---- measurement --------------------------------------------------------
  * Kernel classes timed by the optional profiler (CUDA events recorded on the

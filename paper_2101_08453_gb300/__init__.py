@@ -111,6 +111,7 @@ def lib():
                                     ctypes.c_uint, ctypes.POINTER(Stats), _vp]),
         "mcwind_batch_destroy": (None, [_vp]),
         "mcwind_plan_set_tuning": (_i, [_vp, _i, _i, _i]),
+        "mcwind_plan_wait_selftest": (_i, [_vp, _i, _vp]),
         "mcwind_launch_count": (ctypes.c_longlong, []),
         "mcwind_profile": (_i, [_vp, _i, _vp]),
         "mcwind_profile_read": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_longlong), _i, _vp]),
@@ -376,6 +377,12 @@ def mcwind_residual_norm_noalloc(plan, f, lam, norms, stream=None):
     return _check(lib().mcwind_residual_norm_noalloc(plan, _dev(f, "f"), _dev(lam, "lambda"),
                                                      _dev(norms, "norms"), _stream(stream)),
                   "mcwind_residual_norm_noalloc")
+
+
+def mcwind_plan_wait_selftest(plan, limit_us, stream=None):
+    """Returns the code: MCWIND_ETIMEOUT when the bounded wait ran out (it
+    always does: nothing completes the barrier)."""
+    return lib().mcwind_plan_wait_selftest(plan, int(limit_us), _stream(stream))
 
 
 def mcwind_plan_set_tuning(plan, nu_pre, nu_post, gs_block_rows):

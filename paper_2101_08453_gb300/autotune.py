@@ -33,6 +33,8 @@ def tune_plan(plan, u0, rtol=1e-8, sweeps=SWEEPS, rows=BLOCK_ROWS):
     Returns (best (nu, rows), {candidate: (seconds, cycles, status)})."""
     import torch
     lam = torch.zeros(plan.node_shape, dtype=torch.float64, device="cuda")
+    if plan.options.op_form == 1:
+        rows = (4,)   # the separable form's staged smoother has a fixed block shape
     table = {}
     for nu, r in itertools.product(sweeps, rows):
         mcwind_plan_set_tuning(plan.handle, nu, nu, r)

@@ -1054,19 +1054,50 @@ extern "C" int mcwind_profile_read(mcwind_plan p, double* ms, long long* launche
 }
 
 // ---------------------------------------------------------------------------
-// batches of independent domains
+// batches of independent domains: one CUDA graph per solve
+
+namespace {
+
+// the batch workspace: pointer and handle arrays, then the block read back
+struct BatchLayout {
+  size_t scal, pstat, hif, iter, out, active, cycles, status, nonfinite, nf, hist, total;
+};
+
+BatchLayout batch_layout(int n) {
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  BatchLayout L;
+  size_t o = 0;
+  L.scal = o; o = al(o + 8 * (size_t)n);
+  L.pstat = o; o = al(o + 8 * (size_t)n);
+  L.hif = o; o = al(o + 8 * (size_t)n);
+  L.iter = o; o = al(o + 8);
+  L.out = o;
+  L.active = o; o += 4 * (size_t)n;
+  L.cycles = o; o += 4 * (size_t)n;
+  L.status = o; o += 4 * (size_t)n;
+  L.nonfinite = o; o += 4 * (size_t)n;
+  o = (o + 7) / 8 * 8;
+  L.nf = o; o += 8 * (size_t)n;
+  L.hist = o; o += 8 * (size_t)n * MCWIND_HIST;
+  L.total = al(o);
+  return L;
+}
+
+}  // namespace
 
 struct mcwind_batch_s {
   std::vector<mcwind_plan> plans;
-  double* dres = nullptr;              // device [2n]: ||f||^2, ||r||^2 per domain
-  std::vector<cudaStream_t> streams;   // one per domain
-  cudaStream_t cap = nullptr;
+  char* ws = nullptr;                  // device workspace of the batch
+  BatchLayout lay;
+  std::vector<cudaStream_t> streams;   // one per domain (set-up and output branches)
+  cudaStream_t cap = nullptr;          // the solve's capture stream
+  cudaStream_t body = nullptr;         // capture stream of the loop's bodies
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> joins;
-  // one iteration graph per set of still-active domains (key: '0'/'1' per domain)
-  std::map<std::string, std::pair<cudaGraphExec_t, long long>> graphs;
-  std::vector<const char*> ws_at_capture;
-  std::vector<long long> tuning_at_capture;
+  cudaGraphExec_t exec = nullptr;      // the solve graph
+  std::string key;                     // the arguments it was built for
+  long long fixed_launches = 0;        // kernels outside the loop
+  std::vector<long long> iter_launches;  // kernels of one iteration, per domain
 };
 
 namespace {
@@ -1078,10 +1109,9 @@ long long tuning_key(mcwind_plan p) {
 // fork the batch's domain streams off st, run body(d) on the selected
 // domains, join back into st
 template <typename Body>
-int fork_join(mcwind_batch b, cudaStream_t st, const std::string& active, Body body) {
+int fork_join(mcwind_batch b, cudaStream_t st, Body body) {
   CK(cudaEventRecord(b->fork, st));
   for (size_t d = 0; d < b->plans.size(); ++d) {
-    if (active[d] != '1') continue;
     CK(cudaStreamWaitEvent(b->streams[d], b->fork, 0));
     CKR(body((int)d, b->streams[d]));
     CK(cudaEventRecord(b->joins[d], b->streams[d]));
@@ -1090,60 +1120,161 @@ int fork_join(mcwind_batch b, cudaStream_t st, const std::string& active, Body b
   return MCWIND_OK;
 }
 
-void batch_clear_graphs(mcwind_batch b) {
-  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.first);
-  b->graphs.clear();
+void batch_clear_graph(mcwind_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->key.clear();
 }
 
-// one iteration of the active domains, from the graph cached for that set
-// n V-cycles and a check on the active domains, replayed from the graph of
-// that active set and n
-int batch_iteration(mcwind_batch b, const std::string& active, int n, cudaStream_t st) {
-  bool stale = false;
-  for (size_t d = 0; d < b->plans.size() && !stale; ++d)
-    stale = b->ws_at_capture[d] != b->plans[d]->ws || b->tuning_at_capture[d] != tuning_key(b->plans[d]);
-  if (stale) {
-    batch_clear_graphs(b);
-    for (size_t d = 0; d < b->plans.size(); ++d) {
-      b->ws_at_capture[d] = b->plans[d]->ws;
-      b->tuning_at_capture[d] = tuning_key(b->plans[d]);
-    }
+BatchDev batch_dev(mcwind_batch b, cudaGraphConditionalHandle h_while) {
+  const BatchLayout& L = b->lay;
+  BatchDev v;
+  v.n = (int)b->plans.size();
+  v.scal = (const double* const*)(b->ws + L.scal);
+  v.pstat = (const int* const*)(b->ws + L.pstat);
+  v.h_if = (const cudaGraphConditionalHandle*)(b->ws + L.hif);
+  v.h_while = h_while;
+  v.iter = (int*)(b->ws + L.iter);
+  v.active = (int*)(b->ws + L.active);
+  v.cycles = (int*)(b->ws + L.cycles);
+  v.status = (int*)(b->ws + L.status);
+  v.nonfinite = (int*)(b->ws + L.nonfinite);
+  v.nf = (double*)(b->ws + L.nf);
+  v.hist = (double*)(b->ws + L.hist);
+  return v;
+}
+
+// The solve graph: per-domain set-up, k_batch_step(init), WHILE { per
+// domain IF(active) { cycles_per_check V-cycles + update + float64
+// residual }, k_batch_step(check) }, per-domain output.  Built once per set
+// of arguments (tolerance, cycle limit, flags, buffers, tuning) and replayed.
+int batch_build(mcwind_batch b, const double* const* u0, double* const* lambda, double rtol,
+                int max_cycles, unsigned flags) {
+  const int n = (int)b->plans.size();
+  const int cpc = check_every(b->plans[0]);
+  const int max_checks = max_cycles / cpc;
+  batch_clear_graph(b);
+  std::vector<const double*> sc(n);
+  std::vector<const int*> ps(n);
+  for (int d = 0; d < n; ++d) {
+    sc[d] = scal(b->plans[d]);
+    ps[d] = statusp(b->plans[d]);
   }
-  const std::string key = active + "#" + std::to_string(n);
-  auto it = b->graphs.find(key);
-  if (it == b->graphs.end()) {
-    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    const long long n0 = mcwind_launch_count();
-    const int rc = fork_join(b, b->cap, active, [b, n](int d, cudaStream_t s) -> int {
+  CK(cudaMemcpy(b->ws + b->lay.scal, sc.data(), sizeof(void*) * n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->ws + b->lay.pstat, ps.data(), sizeof(void*) * n, cudaMemcpyHostToDevice));
+  const long long n0 = mcwind_launch_count();
+  CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  cudaGraph_t G = nullptr;
+  std::vector<cudaGraphConditionalHandle> hif(n);
+  cudaGraphConditionalHandle hw = 0;
+  auto body = [&]() -> int {
+    cudaStreamCaptureStatus cs;
+    CK(cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, &G, nullptr, nullptr, nullptr));
+    CK(cudaGraphConditionalHandleCreate(&hw, G, 0, 0));
+    for (int d = 0; d < n; ++d) CK(cudaGraphConditionalHandleCreate(&hif[d], G, 0, 0));
+    const BatchDev dev = batch_dev(b, hw);
+    // per domain: load vector, its norm, first iterate, first float64 residual
+    CKR(fork_join(b, b->cap, [&](int d, cudaStream_t s) -> int {
       mcwind_plan p = b->plans[d];
-      CKR(iteration(p, s, n));
-      CK(cudaMemcpyAsync(b->dres + 2 * d + 1, scal(p) + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
-      return MCWIND_OK;
-    });
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
-    if (rc != MCWIND_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return rc;
+      Level& L0 = p->lv[0];
+      Ptr64 A = lv64(p, 0);
+      CK(rhs_into(p, u0[d], A.f, s));
+      CKR(norm2(p, L0.g, A.f, 0, s));
+      if (flags & MCWIND_WARM)
+        CK(launch_std_to_split<double>(L0.g, lambda[d], A.x, true, s));
+      else
+        CK(cudaMemsetAsync(A.x, 0, sizeof(double) * (size_t)L0.g.total, s));
+      CKR(outer_residual(p, s));
+      return (int)MCWIND_OK;
+    }));
+    CK(launch_batch_step(dev, 0, rtol, max_checks, cpc, b->cap));
+    // the loop node after the init step
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(b->cap, &cs, nullptr, &G, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &wp));
+    CK(cudaStreamUpdateCaptureDependencies(b->cap, &wnode, nullptr, 1,
+                                           cudaStreamSetCaptureDependencies));
+    cudaGraph_t wbody = wp.conditional.phGraph_out[0];
+    std::vector<cudaGraphNode_t> ifs(n);
+    b->iter_launches.assign(n, 0);
+    for (int d = 0; d < n; ++d) {
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = hif[d];
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      CK(cudaGraphAddNode(&ifs[d], wbody, nullptr, nullptr, 0, &ip));
+      const long long k0 = mcwind_launch_count();
+      CK(cudaStreamBeginCaptureToGraph(b->body, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+      const int rc = iteration(b->plans[d], b->body, cpc);
+      cudaGraph_t g_if = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(b->body, &g_if);
+      CKR(rc);
+      CK(e);
+      b->iter_launches[d] = mcwind_launch_count() - k0;
     }
-    CK(e);
-    cudaGraphExec_t exec = nullptr;
-    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    CK(ei);
-    const long long nl = mcwind_launch_count() - n0;
-    count_launches(-(int)nl);
-    it = b->graphs.emplace(key, std::make_pair(exec, nl)).first;
+    CK(cudaStreamBeginCaptureToGraph(b->body, wbody, ifs.data(), nullptr, n,
+                                     cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ec = launch_batch_step(dev, 1, rtol, max_checks, cpc, b->body);
+    cudaGraph_t g_w = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->body, &g_w);
+    CK(ec);
+    CK(ee);
+    // per domain: the solution in the caller's layout
+    CKR(fork_join(b, b->cap, [&](int d, cudaStream_t s) -> int {
+      mcwind_plan p = b->plans[d];
+      CK(launch_split_to_std<double>(p->lv[0].g, lv64(p, 0).x, lambda[d], s));
+      return (int)MCWIND_OK;
+    }));
+    return (int)MCWIND_OK;
+  };
+  const int rc = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+  long long loop_kernels = 1;
+  for (long long k : b->iter_launches) loop_kernels += k;
+  const long long captured = mcwind_launch_count() - n0;
+  count_launches(-(int)captured);  // captured, not run: counted per solve
+  if (rc != MCWIND_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
   }
-  CK(cudaGraphLaunch(it->second.first, st));
-  count_launches((int)it->second.second);
+  CK(e);
+  const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(ei);
+  b->fixed_launches = captured - loop_kernels;
+  CK(cudaMemcpy(b->ws + b->lay.hif, hif.data(), sizeof(cudaGraphConditionalHandle) * n,
+                cudaMemcpyHostToDevice));
   return MCWIND_OK;
+}
+
+std::string batch_key(mcwind_batch b, const double* const* u0, double* const* lambda, double rtol,
+                      int max_cycles, unsigned flags) {
+  std::string k;
+  char buf[64];
+  snprintf(buf, sizeof(buf), "%.17g/%d/%u", rtol, max_cycles, flags);
+  k += buf;
+  for (size_t d = 0; d < b->plans.size(); ++d) {
+    snprintf(buf, sizeof(buf), "|%p,%p,%p,%lld", (const void*)u0[d], (void*)lambda[d],
+             (void*)b->plans[d]->ws, tuning_key(b->plans[d]));
+    k += buf;
+  }
+  return k;
 }
 
 }  // namespace
 
 extern "C" size_t mcwind_batch_workspace_bytes(int n) {
-  return n <= 0 ? 0 : ((size_t)n * 16 + 255) / 256 * 256;
+  return n <= 0 ? 0 : batch_layout(n).total;
 }
 
 extern "C" int mcwind_batch_create(int n, const mcwind_plan* plans, void* workspace,
@@ -1159,10 +1290,10 @@ extern "C" int mcwind_batch_create(int n, const mcwind_plan* plans, void* worksp
   mcwind_batch b = new (std::nothrow) mcwind_batch_s;
   if (!b) return MCWIND_EINVAL;
   b->plans.assign(plans, plans + n);
-  b->dres = (double*)workspace;
-  b->ws_at_capture.assign(n, nullptr);
-  b->tuning_at_capture.assign(n, -1);
+  b->ws = (char*)workspace;
+  b->lay = batch_layout(n);
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   for (int d = 0; d < n && e == cudaSuccess; ++d) {
     cudaStream_t s;
@@ -1185,11 +1316,12 @@ extern "C" int mcwind_batch_create(int n, const mcwind_plan* plans, void* worksp
 
 extern "C" void mcwind_batch_destroy(mcwind_batch b) {
   if (!b) return;
-  batch_clear_graphs(b);
+  batch_clear_graph(b);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->body) cudaStreamDestroy(b->body);
   for (mcwind_plan p : b->plans)
     if (p) p->in_batch = false;
   delete b;
@@ -1207,86 +1339,66 @@ extern "C" int mcwind_batch_solve(mcwind_batch b, const double* const* u0, doubl
     if (b->plans[d]->prof) return MCWIND_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const std::string all(n, '1');
-  // per domain: load vector, its norm, first iterate, first residual
-  CKR(fork_join(b, st, all, [&](int d, cudaStream_t s) -> int {
-    mcwind_plan p = b->plans[d];
-    Level& L0 = p->lv[0];
-    Ptr64 A = lv64(p, 0);
-    CK(rhs_into(p, u0[d], A.f, s));
-    CKR(norm2(p, L0.g, A.f, 0, s));
-    if (flags & MCWIND_WARM)
-      CK(launch_std_to_split<double>(L0.g, lambda[d], A.x, true, s));
-    else
-      CK(cudaMemsetAsync(A.x, 0, sizeof(double) * (size_t)L0.g.total, s));
-    CKR(outer_residual(p, s));
-    CK(cudaMemcpyAsync(b->dres + 2 * d, scal(p), 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    return (int)MCWIND_OK;
-  }));
-  std::vector<double> h(2 * (size_t)n);
-  CK(cudaMemcpyAsync(h.data(), b->dres, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
+  const std::string key = batch_key(b, u0, lambda, rtol, max_cycles, flags);
+  if (!b->exec || key != b->key) {
+    CKR(batch_build(b, u0, lambda, rtol, max_cycles, flags));
+    b->key = key;
+  }
+  // the whole solve: one graph launch, then one read of the bookkeeping
+  CK(cudaGraphLaunch(b->exec, st));
+  const BatchLayout& L = b->lay;
+  std::vector<char> host(L.total - L.out);
+  CK(cudaMemcpyAsync(host.data(), b->ws + L.out, host.size(), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  std::vector<mcwind_stats> S(n);
-  std::vector<double> nf(n);
+  auto at_out = [&](size_t off) { return host.data() + (off - L.out); };
+  const int* cyc = (const int*)at_out(L.cycles);
+  const int* stw = (const int*)at_out(L.status);
+  const int* nfin = (const int*)at_out(L.nonfinite);
+  const double* hist = (const double*)at_out(L.hist);
+  const double* nfv = (const double*)at_out(L.nf);
+  const int cpc = check_every(b->plans[0]);
   int status = MCWIND_OK;
-  bool all_done = true;
+  long long ran = b->fixed_launches;
   for (int d = 0; d < n; ++d) {
-    std::memset(&S[d], 0, sizeof(mcwind_stats));
-    nf[d] = std::sqrt(h[2 * d]);
-    S[d].norm_f = nf[d];
-    if (!std::isfinite(nf[d]) || !std::isfinite(h[2 * d + 1])) status = MCWIND_ENONFINITE;
-    S[d].res_hist[0] = nf[d] > 0.0 ? std::sqrt(h[2 * d + 1]) / nf[d] : 0.0;
-    S[d].cycles = S[d].res_hist[0] <= rtol ? 0 : -1;
-    all_done = all_done && S[d].cycles == 0;
-  }
-  if (status == MCWIND_ENONFINITE) {
-    if (stats)
-      for (int d = 0; d < n; ++d) { S[d].status = MCWIND_ENONFINITE; stats[d] = S[d]; }
-    return status;
-  }
-  int c = 0;
-  std::string active(n, '0');
-  for (int d = 0; d < n; ++d) active[d] = S[d].cycles < 0 ? '1' : '0';
-  const int kc = check_every(b->plans[0]);  // the first domain's setting holds for all
-  while (!all_done && c < max_cycles) {
-    const int nc = std::min(kc, max_cycles - c);
-    CKR(batch_iteration(b, active, nc, st));
-    CK(cudaMemcpyAsync(h.data(), b->dres, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const int c0 = c;
-    c += nc;
-    all_done = true;
-    for (int d = 0; d < n; ++d) {
-      if (S[d].cycles >= 0) continue;
-      S[d].res_hist[c] = nf[d] > 0.0 ? std::sqrt(h[2 * d + 1]) / nf[d] : 0.0;
-      fill_between(S[d].res_hist, c0, c);
-      if (S[d].res_hist[c] <= rtol || !std::isfinite(S[d].res_hist[c])) {
-        S[d].cycles = c;
-        active[d] = '0';
-      } else {
-        all_done = false;
-      }
+    mcwind_stats T;
+    std::memset(&T, 0, sizeof(T));
+    T.cycles = cyc[d];
+    T.norm_f = nfv[d];
+    const double* h = hist + (size_t)d * MCWIND_HIST;
+    for (int c = 0; c <= T.cycles; c += cpc) {
+      T.res_hist[c] = h[c];
+      if (c > 0) fill_between(T.res_hist, c - cpc, c);
     }
-  }
-  for (int d = 0; d < n; ++d) {
-    mcwind_stats& T = S[d];
-    if (T.cycles < 0) T.cycles = c;
+    ran += b->iter_launches[d] * (T.cycles / cpc);
     T.rel_res = T.res_hist[T.cycles];
     if (T.cycles >= 3 && T.res_hist[2] > 0.0)
       T.rate = std::pow(T.res_hist[T.cycles] / T.res_hist[2], 1.0 / (T.cycles - 2));
     else if (T.cycles >= 1 && T.res_hist[0] > 0.0)
       T.rate = std::pow(T.res_hist[T.cycles] / T.res_hist[0], 1.0 / T.cycles);
-    T.status = T.rel_res <= rtol ? MCWIND_OK : MCWIND_ENOTCONV;
-    if (T.status != MCWIND_OK) status = MCWIND_ENOTCONV;
+    if (nfin[d]) {
+      T.status = MCWIND_ENONFINITE;
+      if (status == MCWIND_OK || status == MCWIND_ENOTCONV) status = MCWIND_ENONFINITE;
+    } else {
+      T.status = T.rel_res <= rtol ? MCWIND_OK : MCWIND_ENOTCONV;
+      if (T.status != MCWIND_OK && status == MCWIND_OK) status = MCWIND_ENOTCONV;
+    }
+    if (stw[d] != 0) status = MCWIND_ETIMEOUT;
+    if (stats) stats[d] = T;
   }
-  CKR(fork_join(b, st, all, [&](int d, cudaStream_t s) -> int {
-    mcwind_plan p = b->plans[d];
-    CK(launch_split_to_std<double>(p->lv[0].g, lv64(p, 0).x, lambda[d], s));
-    return (int)MCWIND_OK;
-  }));
-  if (stats)
-    for (int d = 0; d < n; ++d) stats[d] = S[d];
+  int checks = 0;
+  for (int d = 0; d < n; ++d) checks = std::max(checks, cyc[d] / cpc);
+  count_launches((int)(ran + checks));  // set-up + output, the iterations run, the checks
   return status;
+}
+
+extern "C" int mcwind_plan_wait_selftest(mcwind_plan p, int limit_us, void* stream) {
+  if (!p || limit_us < 1 || limit_us > 1000000) return MCWIND_EINVAL;
+  if (!p->assembled) return MCWIND_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_wait_selftest(statusp(p), 1000ull * (unsigned long long)limit_us, st));
+  CK(cudaMemcpyAsync(&p->status_host, statusp(p), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return p->status_host != 0 ? MCWIND_ETIMEOUT : MCWIND_OK;
 }
 
 extern "C" int mcwind_plan_set_tuning(mcwind_plan p, int nu_pre, int nu_post, int gs_block_rows) {

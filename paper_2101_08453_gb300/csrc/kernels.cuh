@@ -175,4 +175,22 @@ cudaError_t launch_residual_sep_staged(const Level& L, bool fuse, const float* H
                                        cudaStream_t st);
 cudaError_t make_tile_maps(Level& L, float* x32, float* f32);
 
+// ---- batch.cu: device bookkeeping of the batched solve (one graph) ----
+struct BatchDev {
+  int n;
+  const double* const* scal;               // per domain: the plan's scalars (0: |f|^2, 1: |r|^2)
+  const int* const* pstat;                 // per domain: the plan's status word
+  const cudaGraphConditionalHandle* h_if;  // per domain: IF handle of its iteration
+  cudaGraphConditionalHandle h_while;      // the solve loop
+  int* iter;                               // checks done
+  int *active, *cycles, *status, *nonfinite;
+  double* nf;                              // ||f_F|| per domain
+  double* hist;                            // [n][MCWIND_HIST] relative residual at the checks
+};
+// a bounded wait that nothing completes (sets the status bit after limit_ns)
+cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st);
+// phase 0: after the set-up (first residuals); phase 1: after one iteration
+cudaError_t launch_batch_step(const BatchDev& b, int phase, double rtol, int max_checks, int cpc,
+                              cudaStream_t st);
+
 }  // namespace mcw

@@ -327,24 +327,40 @@ __global__ void k_vgalerkin(Transfer tr, const double* __restrict__ Vf, double* 
 }
 
 // Expanded 27-point rows from float64 factors into the tiled float64
-// operator (planes 0..26; plane 27 is set by the stencil finalization).
-// One thread per node, blockIdx.z = 2 k + parity.
+// operator (planes 0..26; plane 27 is set by the stencil finalization), in
+// the three-term form: coefficient (s2, dk) = P V_M + R V_K + S A (+ T B on
+// the ground layer's diagonal), S = H_Q - H_Q^T, T = H_Q + H_Q^T,
+// A = (V_G - V_G^T)/2, B = (V_G + V_G^T)/2.  The entries of V_G are dyadic
+// and so are the interpolation weights, so B is exactly -1/2 at (0, 0) and 0
+// elsewhere and A(k, k) is exactly 0: 72 products per node instead of 108.
+// One thread per column (blockIdx.z = parity), walking the layers.
 __global__ void __launch_bounds__(128) k_sep_expand64(Grid g, const double* __restrict__ H,
                                                       const double* __restrict__ V,
                                                       double* __restrict__ C) {
   const int hh = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z >> 1, par = blockIdx.z & 1;
+  const int par = blockIdx.z;
   if (hh >= g.H || j >= g.Ny) return;
   const int64_t col = (int64_t)j * g.RP + (int64_t)par * g.H + hh;
-  const int64_t b = (int64_t)k * g.PP + col;
+  double P[9], S[9], T[9], R[9];
 #pragma unroll
-  for (int s = 0; s < 27; ++s) {
-    const int s2 = s % 9, dk = s / 9;
-    double c = 0.0;
+  for (int s2 = 0; s2 < 9; ++s2) {
+    const double q = H[(9 + s2) * g.PP + col], qt = H[(18 + s2) * g.PP + col];
+    P[s2] = H[s2 * g.PP + col];
+    S[s2] = q - qt;
+    T[s2] = q + qt;
+    R[s2] = H[(27 + s2) * g.PP + col];
+  }
+  for (int k = 0; k < g.Nz; ++k) {
+    const double* v = V + k * kVF;
+    const double Ab = 0.5 * (v[3] - v[6]), Aa = 0.5 * (v[5] - v[8]), Bc = 0.5 * (v[4] + v[7]);
+    const int64_t b = (int64_t)k * g.PP + col;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) c += H[(t * 9 + s2) * g.PP + col] * V[k * kVF + 3 * t + dk];
-    C[cidx(b, s)] = c;
+    for (int s2 = 0; s2 < 9; ++s2) {
+      C[cidx(b, s2)] = fma(S[s2], Ab, fma(P[s2], v[0], R[s2] * v[9]));
+      C[cidx(b, 9 + s2)] = fma(T[s2], Bc, fma(P[s2], v[1], R[s2] * v[10]));
+      C[cidx(b, 18 + s2)] = fma(S[s2], Aa, fma(P[s2], v[2], R[s2] * v[11]));
+    }
   }
 }
 
@@ -770,8 +786,7 @@ cudaError_t launch_vgalerkin(const Transfer& tr, const double* Vf, double* Vc, f
 
 cudaError_t launch_sep_expand64(const Grid& g, const double* H64, const double* V64, double* C,
                                 cudaStream_t st) {
-  k_sep_expand64<<<dim3((g.H + 31) / 32, (g.Ny + 3) / 4, 2 * g.Nz), dim3(32, 4), 0, st>>>(g, H64,
-                                                                                     V64, C);
+  k_sep_expand64<<<dim3((g.H + 31) / 32, (g.Ny + 3) / 4, 2), dim3(32, 4), 0, st>>>(g, H64, V64, C);
   count_launches(1);
   return cudaGetLastError();
 }

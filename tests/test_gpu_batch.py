@@ -1,6 +1,7 @@
-"""Batches of independent domains of uneven sizes (one graph per iteration,
-one branch per domain): every domain's solution against the oracle, the
-batch against one-at-a-time solves, and the autotuner."""
+"""Batches of independent domains of uneven sizes (one graph launch per
+solve: a conditional loop with an IF node per domain): every domain's
+solution against the oracle, the batch against one-at-a-time solves, and
+the autotuner."""
 import numpy as np
 import pytest
 
@@ -20,20 +21,24 @@ def torch():
     return t
 
 
-def make(torch, cases, precision=m.PREC_MIXED):
+def make(torch, cases, precision=m.PREC_MIXED, op_form=m.OP_STORED):
     plans, u0s = [], []
     for c in cases:
         X, Y, Z, u0 = to_dev(torch, c.X, c.Y, c.Z, c.u0)
-        p = m.Plan.for_case(c, precision=precision)
+        p = m.Plan.for_case(c, precision=precision, op_form=op_form)
         p.assemble(X, Y, Z)
         plans.append(p)
         u0s.append(u0)
     return plans, u0s
 
 
-def test_batch_matches_oracle_per_domain(torch):
+@pytest.mark.parametrize("op_form", [m.OP_STORED, m.OP_SEPARABLE])
+def test_batch_matches_oracle_per_domain(torch, op_form):
+    """One graph launch solves every domain (a conditional loop with an IF
+    node per domain): each to the oracle's lambda, and bitwise to its own
+    mcwind_solve."""
     cases = synth.batch_domains(n=7, seed=1, nmin=12, nmax=40, zmin=3, zmax=8)
-    plans, u0s = make(torch, cases)
+    plans, u0s = make(torch, cases, op_form=op_form)
     batch = m.Batch(plans)
     lams, stats = batch.solve(u0s, rtol=1e-11, max_cycles=200)
     for c, lam, st in zip(cases, lams, stats):

@@ -71,12 +71,19 @@ def test_hills_512(torch, a):
     assert rel(lams[m.PREC_MIXED], lams[m.PREC_F64]) <= 1e-6
 
 
-def test_full_domain(torch):
-    """3000 x 3000 x 15 cells (1.44e8 nodes), mixed precision as benchmarked."""
+@pytest.fixture(scope="module")
+def full_case():
     c = synth.full_domain()
-    u0n = synth.perturb_wind(c.u0, 0)
+    return c, synth.perturb_wind(c.u0, 0)
+
+
+@pytest.mark.parametrize("form", [m.OP_SEPARABLE, m.OP_STORED])
+def test_full_domain(torch, full_case, form):
+    """3000 x 3000 x 15 cells (1.44e8 nodes), mixed precision as benchmarked
+    (separable operator), and with the stored operator."""
+    c, u0n = full_case
     X, Y, Z, u0, u0b = to_dev(torch, c.X, c.Y, c.Z, c.u0, u0n)
-    plan = m.Plan.for_case(c, precision=m.PREC_MIXED)
+    plan = m.Plan.for_case(c, precision=m.PREC_MIXED, op_form=form)
     plan.assemble(X, Y, Z)
     lam, st = plan.solve(u0, rtol=1e-8, max_cycles=100)
     assert st.status == m.MCWIND_OK, (st.history(), st.rate)
@@ -119,3 +126,5 @@ def test_full_domain(torch):
                      c.u0[:, :, j0:j0 + w + 1, i0:i0 + w + 1].copy(), c.h1, c.h3)
     u_ref = oracle.recover(sub, lh[:, j0:j0 + w + 1, i0:i0 + w + 1].copy())
     assert np.abs(u[:, :, j0:j0 + w, i0:i0 + w] - u_ref).max() <= 1e-12 * np.abs(u_ref).max()
+    del plan, X, Y, Z, u0, u0b
+    torch.cuda.empty_cache()
