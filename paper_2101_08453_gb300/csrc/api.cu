@@ -37,9 +37,21 @@ int rhs_mode(mcwind_plan p) { return (p->opt.rhs_quad & 1) | (p->opt.u0_at ? 2 :
 bool dfloat_elements(mcwind_plan p) { return p->opt.element_arith == MCWIND_ARITH_DFLOAT; }
 size_t std_nodes(mcwind_plan p) { return (size_t)(p->nx + 1) * (p->ny + 1) * (p->nz + 1); }
 
+// the separable load vector: separable plan, 2x2x2 Gauss with nodal u0,
+// float-pair element arithmetic (MCWIND_ARITH_F64 keeps the element kernel)
+bool sep_rhs(mcwind_plan p) {
+  return p->sep && dfloat_elements(p) && rhs_mode(p) == 0;
+}
+
+int* statusp(mcwind_plan p);
+
 // f (split layout, level 0) = load vector of Eq. 5 from u0
 cudaError_t rhs_into(mcwind_plan p, const double* u0, double* f, cudaStream_t st) {
   const Level& L0 = p->lv[0];
+  if (sep_rhs(p))
+    return launch_rhs_sep(L0, (const float2*)(p->ws + (size_t)L0.R2),
+                          (const float2*)(p->ws + (size_t)L0.VR2), u0,
+                          (float2*)(p->ws + p->off_u2), f, statusp(p), st);
   const float2* xyz2 = (const float2*)(p->ws + p->off_xyz2);
   float2* u2 = (float2*)(p->ws + p->off_u2);
   const bool df = dfloat_elements(p);
@@ -503,7 +515,12 @@ int assemble_separable(mcwind_plan p, cudaStream_t st) {
     PROF(MCWIND_K_SETUP);
     CK(launch_shift_check(Nx, Ny, Nz, p->X, p->Y, p->Z, flagp(p), st));
     CK(launch_hfactors(L0.g, p->X, p->Y, p->Z, p->a, at(p, L0.H64), at(p, L0.H32), flagp(p), st));
-    CK(launch_vfactor0(Nx, Ny, Nz, p->Z, at(p, L0.V64), at(p, L0.V32), flagp(p), st));
+    CK(launch_vfactor0(Nx, Ny, Nz, p->Z, at(p, L0.V64), at(p, L0.V32), at(p, L0.VR2), flagp(p),
+                       st));
+    if (sep_rhs(p)) {
+      CK(launch_rhs_factors(L0.g, p->X, p->Y, p->Z, at(p, L0.R2), st));
+      CK(make_u0_map(L0, (float2*)(p->ws + p->off_u2)));
+    }
   }
   {
     // the finest float64 rows (the refinement's residual operator): the same

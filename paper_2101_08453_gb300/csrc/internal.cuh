@@ -133,6 +133,18 @@ constexpr int kVF = 12;
 __host__ __device__ constexpr int64_t hidx(int64_t col, int q) {
   return ((col >> 5) * kHF + q) * 32 + (col & 31);
 }
+// Load vector of Eq. 5 on a shift-form grid (2x2x2 Gauss, nodal u0):
+//   f = -[(E_x (x) V_M) u_x + (E_y (x) V_M) u_y - (F_x (x) V_G^T) u_x
+//         - (F_y (x) V_G^T) u_y + (M_z (x) V_G^T) u_z]
+// with five horizontal 9-point factors per column (no coupling zeroed: f at a
+// free node takes u0 at every node around it) kept as float pairs in tiles
+// of 32 columns (term q = 9 t + s2, t = E_x, E_y, F_x, F_y, M_z), and per
+// layer V_M(k, k-1..k+1), V_G^T(k, k-1..k+1) as float pairs.
+constexpr int kRF = 45;
+constexpr int kRV = 6;
+__host__ __device__ constexpr int64_t ridx(int64_t col, int q) {
+  return ((col >> 5) * kRF + q) * 32 + (col & 31);
+}
 
 struct Level {
   Grid g;
@@ -146,11 +158,14 @@ struct Level {
   float* H32 = nullptr;
   double* V64 = nullptr;
   float* V32 = nullptr;
+  float2* R2 = nullptr;      // finest level: load-vector factors (float pairs)
+  float2* VR2 = nullptr;     // finest level: their vertical factors
   bool h_shared = false;
   bool has_c64 = true;     // false: separable form on an intermediate level
   // separable form: tensor maps of x32 and f32 as [Nz][Ny][2][H] float tiles
   // for the staged smoother (built at assembly, tied to the workspace)
   CUtensorMap tm_x, tm_f, tm_rx, tm_rf;
+  CUtensorMap tm_u;   // finest level: u0 pairs, split layout, 3 components
   double *x64 = nullptr, *f64 = nullptr, *r64 = nullptr;
   float *x32 = nullptr, *f32 = nullptr, *r32 = nullptr;
   // host description of the transfer to the next level

@@ -151,7 +151,15 @@ cudaError_t launch_hgalerkin(int dim, const Grid& gin, const Grid& gout, const d
                              double* Hout, cudaStream_t st);
 // finest vertical factors from column (0, 0) of Z; Galerkin to the next level
 cudaError_t launch_vfactor0(int Nx, int Ny, int Nz, const double* Z, double* V64, float* V32,
-                            int* flag, cudaStream_t st);
+                            float2* VR2, int* flag, cudaStream_t st);
+// ---- sep_rhs.cu: the load vector of Eq. 5 from column x layer factors ----
+cudaError_t launch_rhs_factors(const Grid& g, const double* X, const double* Y, const double* Z,
+                               float2* R2, cudaStream_t st);
+cudaError_t make_u0_map(Level& L, float2* u2);
+// u0 -> float pairs in the split layout (u2, 3 x g.total), then f (split layout,
+// float64, 0 at fixed nodes)
+cudaError_t launch_rhs_sep(const Level& L, const float2* R2, const float2* VR2, const double* u0,
+                           float2* u2, double* f, int* status, cudaStream_t st);
 cudaError_t launch_vgalerkin(const Transfer& tr, const double* Vf, double* Vc, float* Vc32,
                              cudaStream_t st);
 // 27-point rows from float64 factors into a tiled float64 operator (planes 0..26)

@@ -185,6 +185,10 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
       }
       L.V64 = (double*)off; off = align256(off + (size_t)kVF * L.g.Nz * 8);
       L.V32 = (float*)off; off = align256(off + (size_t)kVF * L.g.Nz * 4);
+      if (l == 0) {
+        L.R2 = (float2*)off; off = align256(off + (size_t)kRF * L.g.PP * 8);
+        L.VR2 = (float2*)off; off = align256(off + (size_t)kRV * L.g.Nz * 8);
+      }
     }
     L.x64 = (double*)off; off = align256(off + t * 8);
     L.f64 = (double*)off; off = align256(off + t * 8);
@@ -236,8 +240,8 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
     const size_t nodes = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
     p->off_xyz2 = off;
     off = align256(off + 3 * nodes * sizeof(float2));
-    p->off_u2 = off;
-    off = align256(off + 3 * nodes * sizeof(float2));
+    p->off_u2 = off;  // nodal u0 as float pairs: [k][j][i], or the split layout (separable)
+    off = align256(off + 3 * std::max(nodes, (size_t)p->lv[0].g.total) * sizeof(float2));
   }
   p->n_adj = adjoint_partials(nx, ny, nz);
   p->off_adj = off;

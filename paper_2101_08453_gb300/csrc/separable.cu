@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include "async.cuh"
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace mcw {
@@ -261,7 +262,8 @@ __global__ void __launch_bounds__(128) k_hgalerkin(Grid gin, Grid gout,
 // kappa to layers l, l+1.  One thread.  Couplings to the top layer (fixed)
 // are zero.
 __global__ void k_vfactor0(int Nx, int Ny, int Nz, const double* __restrict__ Z,
-                           double* __restrict__ V, float* __restrict__ V32, int* flag) {
+                           double* __restrict__ V, float* __restrict__ V32, float2* __restrict__ VR,
+                           int* flag) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   const int64_t lay = (int64_t)Nx * Ny;
   for (int q = 0; q < Nz * kVF; ++q) V[q] = 0.0;
@@ -278,6 +280,14 @@ __global__ void k_vfactor0(int Nx, int Ny, int Nz, const double* __restrict__ Z,
     // term 3: (2/h) [[1,-1],[-1,1]]/2
     lo[9 + 1] += 1.0 / h; lo[9 + 2] -= 1.0 / h; up[9 + 0] -= 1.0 / h; up[9 + 1] += 1.0 / h;
   }
+  // the load vector's vertical factors, V_M and V_G^T with the top layer
+  // kept (u0 of the top nodes enters the rows below them)
+  if (VR)
+    for (int k = 0; k < Nz; ++k)
+      for (int d = 0; d < 3; ++d) {
+        VR[k * kRV + d] = split_bits(V[k * kVF + d]);
+        VR[k * kRV + 3 + d] = split_bits(V[k * kVF + 6 + d]);
+      }
   for (int t = 0; t < 4; ++t) {
     V[(Nz - 2) * kVF + 3 * t + 2] = 0.0;
     for (int d = 0; d < 3; ++d) V[(Nz - 1) * kVF + 3 * t + d] = 0.0;
@@ -771,8 +781,8 @@ cudaError_t launch_hgalerkin(int dim, const Grid& gin, const Grid& gout, const d
 }
 
 cudaError_t launch_vfactor0(int Nx, int Ny, int Nz, const double* Z, double* V64, float* V32,
-                            int* flag, cudaStream_t st) {
-  k_vfactor0<<<1, 32, 0, st>>>(Nx, Ny, Nz, Z, V64, V32, flag);
+                            float2* VR2, int* flag, cudaStream_t st) {
+  k_vfactor0<<<1, 32, 0, st>>>(Nx, Ny, Nz, Z, V64, V32, VR2, flag);
   count_launches(1);
   return cudaGetLastError();
 }

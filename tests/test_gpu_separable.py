@@ -74,6 +74,18 @@ def test_separable_stencil_all_levels(torch, name):
 
 
 @pytest.mark.parametrize("name", SHIFT)
+@pytest.mark.parametrize("quad", [m.RHS_GAUSS8, m.RHS_CENTER1])
+def test_separable_rhs(torch, name, quad):
+    """The load vector of Eq. 5: from column x layer factors in float pairs
+    (2x2x2 Gauss, nodal u0), element by element for the one-point rule."""
+    c, plan, (X, Y, Z, u0), _ = setup(torch, name, rhs_quad=quad)
+    f = plan.rhs(u0).cpu().numpy().ravel()
+    ref = oracle.assemble_f(c, quad=quad)
+    ref[~oracle.case_free_mask(c)] = 0.0
+    assert np.abs(f - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", SHIFT)
 def test_separable_residual(torch, name):
     c, plan, _, H = setup(torch, name)
     rng = np.random.default_rng(1)
