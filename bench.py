@@ -45,6 +45,13 @@ SAMPLE_I0, SAMPLE_J0 = 1420, 1420
 # arithmetic the method needs, the `alu` roofline's numerator.
 FP32_OPS_STIFFNESS = 14198.0
 FP32_OPS_LOAD = 8308.0
+# Center recovery in float pairs: FMA-pipe thread instructions per element of
+# this build, counted by ncu on the 600x600x15 case (86 % of its instructions;
+# the FMA pipe was 73 % busy), the `alu` units of the recover class.
+FP32_OPS_RECOVER = 1811.0
+# Separable load vector: float-pair multiply-adds per node (45 horizontal and
+# 6 vertical), about 12 FP32-pipe instructions each.
+FP32_OPS_LOAD_SEPARABLE = 51 * 12.0
 # FP32 pipe: 128 lanes per SM x 152 SMs x 2.07 GHz maximum SM clock
 FP32_PIPE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per unit of a launch, from one ncu capture of the
@@ -274,7 +281,7 @@ def read_profile(m, plan):
     return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}
 
 
-def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse):
+def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep_rhs=True):
     """Algorithmic units of every kernel class over the timed region.
 
     levels: the plan's level descriptions (Nx, Ny, Nz, hx, hy); solves: the
@@ -343,10 +350,55 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse):
             add(k, "hbm", hb[k])
         if fp64[k]:
             add(k, "fp64", fp64[k])
-    # per call: load vector (2 per step), recovery (2 per step), assembly (1 per step)
-    U["rhs"] = [["alu", nsolve * FP32_OPS_LOAD * n_elem]]
-    U["assemble"] = [["alu", nsolve / 2 * FP32_OPS_STIFFNESS * n_elem]]
-    U["recover"] = [["hbm", nsolve * ((8 + 24 + 24) * nodes[0] + 24.0 * n_elem)]]
+    # per call: load vector (one per solve), recovery (one per solve), assembly
+    # (one per two solves)
+    if separable and sep_rhs:
+        # u0 -> split-layout float pairs (24 B in, 24 B out per node), then the
+        # load vector: u0 pairs in, f out, the column factors once
+        U["rhs"] = [["hbm", nsolve * (48 + 24 + 8) * nodes[0] + nsolve * 45 * 8.0 * fcols[0]],
+                    ["alu", nsolve * FP32_OPS_LOAD_SEPARABLE * nodes[0]]]
+    else:
+        U["rhs"] = [["alu", nsolve * FP32_OPS_LOAD * n_elem]]
+    if separable:
+        # the finest float64 rows from the factors (72 float64 FMAs per node, the
+        # 27 coefficients written) and the coordinates split into float pairs
+        U["assemble"] = [["fp64", nsolve / 2 * 72.0 * nodes[0]],
+                         ["hbm", nsolve / 2 * (27 * 8 + 48) * nodes[0]]]
+    else:
+        U["assemble"] = [["alu", nsolve / 2 * FP32_OPS_STIFFNESS * n_elem]]
+    U["recover"] = [["hbm", nsolve * ((8 + 24 + 24) * nodes[0] + 24.0 * n_elem)],
+                    ["alu", nsolve * FP32_OPS_RECOVER * n_elem]]
+    # Galerkin products per assembly: of the column factors (separable: 36 float64
+    # values per column read and written per horizontal stage, and the float32
+    # tiles), or of the stored rows (28 float64 values per node in and out per
+    # one-direction stage)
+    n_asm = nsolve / 2
+    rap = 0.0
+    for l in range(L - 1):
+        a, b = levels[l], levels[l + 1]
+        if separable:
+            if a["hx"] or a["hy"]:
+                cin = a["Nx"] * a["Ny"]
+                cmid = b["Nx"] * a["Ny"] if (a["hx"] and a["hy"]) else 0
+                cout = b["Nx"] * b["Ny"]
+                rap += 36 * 8.0 * (cin + 2 * cmid + cout) + 36 * 12.0 * cout
+        else:
+            stages = int(a["hx"]) + int(a["hy"]) + int(b["Nz"] != a["Nz"])
+            rap += stages * 28 * 8.0 * (nodes[l] + nodes[l + 1])
+    U["rap"] = [["hbm", n_asm * rap]]
+    # set-up per assembly: the finest rows' finalization (27 coefficients read,
+    # 1/diag written) and, separable, the shift-form check (X, Y, Z read) and
+    # the two float64 factor passes over the ground layer
+    setup = (27 * 8 + 8) * nodes[0]
+    if separable:
+        setup += 24 * nodes[0] + (36 + 45) * 8 * 2.0 * fcols[0]
+    elif mixed:
+        setup += sum(28 * 12.0 * nn for nn in nodes)  # float32 copies
+    U["setup"] = [["hbm", n_asm * setup]]
+    # layout conversions and norms per solve: |f| (8 B per node), lambda out
+    # (8 in, 8 out), lambda in for warm starts; per recovery lambda and u0 split
+    # into float pairs (16 and 48 B per node)
+    U["other"] = [["hbm", nsolve * (8 + 16 + 16 + 64) * nodes[0] - nsolve / 2 * 16 * nodes[0]]]
     return {k: v for k, v in U.items() if v}
 
 
