@@ -285,7 +285,7 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep
     """Algorithmic units of every kernel class over the timed region.
 
     levels: the plan's level descriptions (Nx, Ny, Nz, hx, hy); solves: the
-    cycle counts of the timed solves.  For each class a list of (bound, total
+    cycle counts of the timed solves (cold and warm alternating, cold first).  For each class a list of (bound, total
     units): bytes every array element the launches must read or write at
     least once ("hbm"), float64 FMAs ("fp64"), float-pair FP32-pipe operations
     ("alu").  A smoother launch of one column group reads the x values of the
@@ -338,12 +338,26 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep
         if not fused:
             hb["restrict"] += cycles * (cs * nodes[l] + cs * nodes[l + 1])
         hb["prolong"] += cycles * (cs * nodes[l + 1] + 2 * cs * free[l])
+        if not mixed:
+            # float64 transfers: per fine node its n coarse taps share one
+            # weight, n float64 operations; per coarse node centre + (minus +
+            # plus) / 2 per direction and row, two operations each
+            a, b = levels[l], levels[l + 1]
+            tx = (a["Nx"] - 2) + (-(-(a["Nx"] - 2) // 2) if a["hx"] else 0)
+            ty = (a["Ny"] - 2) + (-(-(a["Ny"] - 2) // 2) if a["hy"] else 0)
+            tz = (a["Nz"] - 1) + (a["Nz"] - b["Nz"])
+            fp64["prolong"] += cycles * float(tx) * ty * tz
+            rows = (3 if a["hy"] else 1) * 3
+            per_c = 2 * (rows if a["hx"] else 0) + 2 * (3 if a["hy"] else 0) + 2
+            fp64["restrict"] += cycles * float(per_c) * free[l + 1]
     hb["coarse_solve"] += cycles * 8.0 * n_coarse * n_coarse
     fp64["coarse_solve"] += cycles * float(n_coarse) * n_coarse
     if mixed:
         hb["update"] += checks * 20.0 * free[0]
-    n_outer = checks + nsolve
-    hb["outer_residual"] += n_outer * (27 * 8 + 8 + 8 + (8 if mixed else 8)) * free[0]
+    # the first residual of a cold solve is r = f (x = 0): f read, r written
+    n_cold = (nsolve + 1) // 2
+    n_outer = checks + nsolve - n_cold
+    hb["outer_residual"] += n_outer * (27 * 8 + 8 + 8 + 8) * free[0] + n_cold * 16.0 * free[0]
     fp64["outer_residual"] += n_outer * 28.0 * free[0]
     for k in U:
         if hb[k]:
@@ -360,10 +374,9 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep
     else:
         U["rhs"] = [["alu", nsolve * FP32_OPS_LOAD * n_elem]]
     if separable:
-        # the finest float64 rows from the factors (72 float64 FMAs per node, the
-        # 27 coefficients written) and the coordinates split into float pairs
-        U["assemble"] = [["fp64", nsolve / 2 * 72.0 * nodes[0]],
-                         ["hbm", nsolve / 2 * (27 * 8 + 48) * nodes[0]]]
+        # the finest float64 rows expanded from the factors in float pairs: 27
+        # coefficients and 1/diag written per node, the column factors read once
+        U["assemble"] = [["hbm", nsolve / 2 * (28 * 8.0 * nodes[0] + 36 * 8.0 * nodes[0] / levels[0]["Nz"])]]
     else:
         U["assemble"] = [["alu", nsolve / 2 * FP32_OPS_STIFFNESS * n_elem]]
     U["recover"] = [["hbm", nsolve * ((8 + 24 + 24) * nodes[0] + 24.0 * n_elem)],
@@ -615,7 +628,7 @@ def main():
     X, Y, Z, U0, U0N = (torch.from_numpy(a).to(dev) for a in (case.X, case.Y, case.Z, case.u0, u0n_np))
     op_form = m.OP_SEPARABLE if (args.op_form == "separable" and prec == m.PREC_MIXED) else m.OP_STORED
     plan = m.Plan.for_case(case, precision=prec, op_form=op_form)
-    plan_cpc = plan.options.cycles_per_check
+    plan_cpc = m.plan_options(plan.handle).cycles_per_check   # the interval in use
     plan_ws = plan.workspace_bytes
     plan_nu = (plan.options.nu_pre, plan.options.nu_post)
     main_levels = [plan.level(l) for l in range(plan.num_levels)]
@@ -834,7 +847,7 @@ def main():
         return [p.level(l) for l in range(p.num_levels)]
 
     mixed = prec == m.PREC_MIXED
-    cpc = plan_cpc or (2 if mixed else 1)
+    cpc = plan_cpc
     timed_solves = [c for cyc in cycles for c in cyc[:2]]
     lev_main = main_levels
     nc_main = ((lev_main[-1]["Nx"] - 2) * (lev_main[-1]["Ny"] - 2) * (lev_main[-1]["Nz"] - 1))
@@ -888,7 +901,7 @@ def main():
                    "l2": "inputs larger than L2 (X, Y, Z, u0, u0' = %.1f GB resident)" % (
                        9 * n_nodes * 8 / 1e9),
                    "replicas": world,
-                   "cycles_per_check": (plan_cpc or (2 if prec == m.PREC_MIXED else 1))},
+                   "cycles_per_check": plan_cpc},
         "gpu_launches": int(launches),
         "cycles_per_step": {"cold": cycles[-1][0], "warm": cycles[-1][1]},
         "rel_res": {"cold": cycles[-1][2], "warm": cycles[-1][3]},

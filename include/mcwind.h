@@ -128,16 +128,22 @@ typedef struct {
      The Galerkin products of the coarser levels sum in float pairs either
      way (their interpolation weights make every product exact); the stored
      operators and the solve are float64 (float32 inside the float64
-     refinement of MCWIND_PREC_MIXED). */
+     refinement of MCWIND_PREC_MIXED).  With MCWIND_OP_SEPARABLE the same
+     choice applies to the column factors' Gauss sums, the finest and
+     coarsest float64 rows expanded from the factors, and the load vector
+     (float pairs from its own factors; float64 element by element). */
   int element_arith;
-  /* V-cycles between two convergence checks, 1..8; 0 (default) = 2 with
-     MCWIND_PREC_MIXED, 1 with MCWIND_PREC_F64.  In mixed precision the
-     cycles of one check run back to back on the float32 correction (the
-     second from the first one's result, as in the plain multigrid
-     iteration) before the float64 update and residual, which are computed
-     once per check.  Solves stop at a check, so the cycle count is a
-     multiple of this (or max_cycles).  Ignored with MCWIND_ACCEL_CG (one
-     cycle per iteration). */
+  /* V-cycles between two convergence checks, 1..8; 0 (default) = 6 with
+     MCWIND_PREC_MIXED, 1 with MCWIND_PREC_F64 (mcwind_plan_query reports
+     the value in use).  In mixed precision the cycles of one check run back
+     to back on the float32 correction (each from the previous one's result,
+     as in the plain multigrid iteration) before the float64 update and
+     residual, which are computed once per check: a float64 residual costs
+     about as much as a float32 cycle on GB300 (its 27 multiply-adds per node
+     run at the float64 rate), and the float32 correction keeps converging
+     for 6 cycles on the benchmark's grids.  Solves stop at a check, so the
+     cycle count is a multiple of this (or max_cycles).  Ignored with
+     MCWIND_ACCEL_CG (one cycle per iteration). */
   int cycles_per_check;
   /* Form of the float32 cycle's operators (MCWIND_PREC_MIXED).
      MCWIND_OP_STORED (default): the 27 coefficients of every node are stored
@@ -182,8 +188,9 @@ int mcwind_plan_create(int nx, int ny, int nz, const double a[3], double h1, con
                        const mcwind_options* opt, mcwind_plan* out, size_t* workspace_bytes);
 
 /* The plan's options as they stand (host output; mcwind_plan_set_tuning
- * changes nu_pre and nu_post) and its device workspace bytes.  Either output
- * may be NULL.  Host only.  EINVAL on a NULL plan. */
+ * changes nu_pre and nu_post; a cycles_per_check of 0 is reported as the
+ * interval in use) and its device workspace bytes.  Either output may be
+ * NULL.  Host only.  EINVAL on a NULL plan. */
 int mcwind_plan_query(mcwind_plan plan, mcwind_options* opt, size_t* workspace_bytes);
 
 /* Number of grid levels (finest = 0); negative code on a NULL plan. */

@@ -173,9 +173,8 @@ template <typename T>
 constexpr bool is_f32() { return sizeof(T) == 4; }
 
 double* dense_inv(mcwind_plan p) {
-  // result of the Gauss-Jordan ping-pong: n even -> first buffer, odd -> second
-  double* A = (double*)(p->ws + p->off_dense);
-  return (p->n_coarse % 2 == 0) ? A : A + (size_t)p->n_coarse * p->n_coarse;
+  // the blocked Gauss-Jordan inverts in place, in the first buffer
+  return (double*)(p->ws + p->off_dense);
 }
 
 // sweeps of the column Gauss-Seidel smoother on level l; zero_start: x is 0
@@ -283,17 +282,20 @@ int norm2(mcwind_plan p, const Grid& g, const double* v, int slot, cudaStream_t 
 
 // residual of the outer float64 iteration on level 0 and its squared norm in scal[1];
 // in mixed mode also the float32 right side and a zero start of the correction.
-int outer_residual(mcwind_plan p, cudaStream_t st) {
+// x_zero: the iterate is known to be 0 (a cold start), so r = f without a
+// product (the same values and norm as the full residual).
+int outer_residual(mcwind_plan p, cudaStream_t st, bool x_zero = false) {
   Ptr64 A = lv64(p, 0);
   const Grid& g = p->lv[0].g;
+  const double* x = x_zero ? nullptr : A.x;
   int nb = 0;
   {
     PROF(MCWIND_K_OUTER_RESIDUAL);
     if (p->opt.precision == MCWIND_PREC_F64) {
-      CK(launch_residual<double>(g, A.C, A.f, A.x, A.r, partials(p), p->n_partials, &nb, st));
+      CK(launch_residual<double>(g, A.C, A.f, x, A.r, partials(p), p->n_partials, &nb, st));
     } else {
       Ptr32 B = lv32(p, 0);
-      CK(launch_residual_mixed(g, A.C, A.f, A.x, B.f, B.x, partials(p), p->n_partials, &nb, st));
+      CK(launch_residual_mixed(g, A.C, A.f, x, B.f, B.x, partials(p), p->n_partials, &nb, st));
     }
   }
   PROF(MCWIND_K_OTHER);
@@ -302,10 +304,7 @@ int outer_residual(mcwind_plan p, cudaStream_t st) {
 }
 
 // V-cycles between two convergence checks (the option, or its default)
-int check_every(mcwind_plan p) {
-  if (p->opt.cycles_per_check > 0) return p->opt.cycles_per_check;
-  return p->opt.precision == MCWIND_PREC_MIXED ? 2 : 1;
-}
+int check_every(mcwind_plan p) { return effective_cycles_per_check(p->opt); }
 
 // n V-cycles, then the float64 residual and its norm (one check).  Mixed
 // precision: the cycles iterate on the float32 correction (the first from
@@ -429,7 +428,9 @@ extern "C" int mcwind_assemble(mcwind_plan p, void* workspace, const double* X, 
     PROF(MCWIND_K_ASSEMBLE);
     float2* xyz2 = (float2*)(p->ws + p->off_xyz2);
     const int64_t nn = (int64_t)std_nodes(p);
-    if (dfloat_elements(p)) {
+    // the element kernels' coordinates as float pairs (a separable plan
+    // needs them only for a load vector formed element by element)
+    if (dfloat_elements(p) && (!p->sep || !sep_rhs(p))) {
       CK(launch_split_pairs(X, xyz2, nn, st));
       CK(launch_split_pairs(Y, xyz2 + nn, nn, st));
       CK(launch_split_pairs(Z, xyz2 + 2 * nn, nn, st));
@@ -514,7 +515,8 @@ int assemble_separable(mcwind_plan p, cudaStream_t st) {
   {
     PROF(MCWIND_K_SETUP);
     CK(launch_shift_check(Nx, Ny, Nz, p->X, p->Y, p->Z, flagp(p), st));
-    CK(launch_hfactors(L0.g, p->X, p->Y, p->Z, p->a, at(p, L0.H64), at(p, L0.H32), flagp(p), st));
+    CK(launch_hfactors(L0.g, p->X, p->Y, p->Z, p->a, at(p, L0.H64), at(p, L0.H32), flagp(p),
+                       dfloat_elements(p), st));
     CK(launch_vfactor0(Nx, Ny, Nz, p->Z, at(p, L0.V64), at(p, L0.V32), at(p, L0.VR2), flagp(p),
                        st));
     if (sep_rhs(p)) {
@@ -526,11 +528,8 @@ int assemble_separable(mcwind_plan p, cudaStream_t st) {
     // the finest float64 rows (the refinement's residual operator): the same
     // 2x2x2-Gauss stiffness, assembled from its column and layer factors
     PROF(MCWIND_K_ASSEMBLE);
-    CK(launch_sep_expand64(L0.g, at(p, L0.H64), at(p, L0.V64), at(p, L0.C64), st));
-  }
-  {
-    PROF(MCWIND_K_SETUP);
-    CK(launch_stencil_finalize(L0.g, at(p, L0.C64), flagp(p), st));
+    CK(launch_sep_expand64(L0.g, at(p, L0.H64), at(p, L0.V64), at(p, L0.C64), flagp(p),
+                           dfloat_elements(p), st));
   }
   for (size_t l = 0; l < p->lv.size(); ++l)
     CK(make_tile_maps(p->lv[l], at(p, p->lv[l].x32), at(p, p->lv[l].f32)));
@@ -551,8 +550,8 @@ int assemble_separable(mcwind_plan p, cudaStream_t st) {
   }
   Level& Lc = p->lv.back();
   PROF(MCWIND_K_SETUP);
-  CK(launch_sep_expand64(Lc.g, at(p, Lc.H64), at(p, Lc.V64), at(p, Lc.C64), st));
-  CK(launch_stencil_finalize(Lc.g, at(p, Lc.C64), flagp(p), st));
+  CK(launch_sep_expand64(Lc.g, at(p, Lc.H64), at(p, Lc.V64), at(p, Lc.C64), flagp(p),
+                         dfloat_elements(p), st));
   return MCWIND_OK;
 }
 
@@ -741,7 +740,7 @@ static int solve_impl(mcwind_plan p, const double* u0, const double* f_given, do
     else
       CK(cudaMemsetAsync(A.x, 0, sizeof(double) * (size_t)L0.g.total, st));
   }
-  CKR(outer_residual(p, st));
+  CKR(outer_residual(p, st, !(flags & MCWIND_WARM)));
   double h[2];
   CKR(read_scalars(p, h, 0, 2, st));
   const double nf = std::sqrt(h[0]);
@@ -839,6 +838,14 @@ extern "C" int mcwind_recover(mcwind_plan p, const double* u0, const double* lam
   if (!p->assembled) return MCWIND_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;
   Level& L0 = p->lv[0];
+  if (where == MCWIND_AT_CENTERS && dfloat_elements(p) && p->sep) {
+    // shift form: the column's center Jacobian once, each layer's 2/h
+    const bool nodal = p->opt.u0_at == MCWIND_U0_NODES;
+    PROF(MCWIND_K_RECOVER);
+    CK(launch_recover_center_sep(p->nx, p->ny, p->nz, p->X, p->Y, p->Z, nodal ? u0 : nullptr,
+                                 nodal ? nullptr : u0, lambda, p->a, u, st));
+    return MCWIND_OK;
+  }
   if (where == MCWIND_AT_CENTERS && dfloat_elements(p)) {
     // float pairs: lambda and a nodal u0 split in the [k][j][i] layout
     float2* lam2 = (float2*)lv64(p, 0).r;  // scratch, >= nodes float pairs
@@ -1201,7 +1208,7 @@ int batch_build(mcwind_batch b, const double* const* u0, double* const* lambda, 
         CK(launch_std_to_split<double>(L0.g, lambda[d], A.x, true, s));
       else
         CK(cudaMemsetAsync(A.x, 0, sizeof(double) * (size_t)L0.g.total, s));
-      CKR(outer_residual(p, s));
+      CKR(outer_residual(p, s, !(flags & MCWIND_WARM)));
       return (int)MCWIND_OK;
     }));
     CK(launch_batch_step(dev, 0, rtol, max_checks, cpc, b->cap));

@@ -69,16 +69,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
+// try_wait with an explicit suspend-time hint: the thread may sleep in
+// hardware until the phase completes or about hint_ns pass, so a waiting
+// warp issues no instructions meanwhile
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+
+// suspend-time hint of one try in the bounded waits below (far below the
+// wall-clock limit, far above a tile's arrival time)
+constexpr uint32_t kWaitHintNs = 20000;
+
 // Wait for the phase of the given parity to complete, at most limit_ns;
 // on timeout set kStatusWaitTimeout in *status and return false.
 __device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity, int* status,
                                             unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
-  // try_wait suspends the thread in hardware until the phase completes or a
-  // short time limit passes, so the loop needs no sleep of its own
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_hint(bar, parity, kWaitHintNs)) return true;
     if (global_timer_ns() - t0 > limit_ns) {
       atomicOr(status, kStatusWaitTimeout);
       return false;

@@ -2,8 +2,9 @@
 // The free block of the coarsest operator (n <= 4096 unknowns, numbered
 // k-major over the free nodes) is gathered into a dense matrix and inverted
 // once, at assembly, by Gauss-Jordan elimination without pivoting (the
-// matrix is symmetric positive definite), one launch per pivot.  Each cycle
-// then applies the inverse as a dense matrix-vector product in float64.
+// matrix is symmetric positive definite) in blocks of kGjB pivots, three
+// launches per block.  Each cycle then applies the inverse as a dense
+// matrix-vector product in float64.
 #include "kernels.cuh"
 
 namespace mcw {
@@ -30,19 +31,72 @@ __global__ void k_dense_gather(Grid g, const double* __restrict__ C, int n,
   A[(int64_t)row * n + col] = C[cidx(gidx(g, i, j, k), s)];
 }
 
-__global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, int n, int p) {
-  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// Blocked Gauss-Jordan in the exchange form: with the pivot block P of b
+// indices and the others O, one block step maps
+//   A_PP -> A_PP^-1,  A_PO -> A_PP^-1 A_PO,  A_OP -> -A_OP A_PP^-1,
+//   A_OO -> A_OO - A_OP A_PP^-1 A_PO,
+// which equals b single-pivot steps; after all blocks A holds A^-1.  The
+// Schur complements of an SPD matrix stay SPD, so no pivoting is needed.
+constexpr int kGjB = 16;
+
+// the pivot block's inverse (b x b) by scalar Gauss-Jordan in shared memory
+__global__ void __launch_bounds__(256) k_gj_pivot(const double* __restrict__ A, int n, int p0,
+                                                  int b, double* __restrict__ Pinv) {
+  __shared__ double M[kGjB][kGjB];
+  const int t = threadIdx.x, r = t / kGjB, c = t % kGjB;
+  if (r < b && c < b) M[r][c] = A[(int64_t)(p0 + r) * n + p0 + c];
+  __syncthreads();
+  for (int p = 0; p < b; ++p) {
+    double v = 0.0;
+    if (r < b && c < b) {
+      const double ip = 1.0 / M[p][p];
+      if (r == p && c == p) v = ip;
+      else if (r == p) v = M[p][c] * ip;
+      else if (c == p) v = -M[r][p] * ip;
+      else v = M[r][c] - M[r][p] * (M[p][c] * ip);
+    }
+    __syncthreads();
+    if (r < b && c < b) M[r][c] = v;
+    __syncthreads();
+  }
+  if (r < b && c < b) Pinv[r * kGjB + c] = M[r][c];
+}
+
+// U = A_PP^-1 A_P. (b rows, all columns) and Lo = A_.P (all rows, the b
+// pivot columns, before the step): one thread per (row, pivot) pair of each
+__global__ void k_gj_panel(const double* __restrict__ A, int n, int p0, int b,
+                           const double* __restrict__ Pinv, double* __restrict__ U,
+                           double* __restrict__ Lo) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= (int64_t)b * n) return;
+  const int t = (int)(q / n), c = (int)(q % n);
+  double s = 0.0;
+  for (int u = 0; u < b; ++u) s += Pinv[t * kGjB + u] * A[(int64_t)(p0 + u) * n + c];
+  U[(int64_t)t * n + c] = s;
+  Lo[(int64_t)c * kGjB + t] = A[(int64_t)c * n + p0 + t];
+}
+
+// the block step on every entry, from the saved panels
+__global__ void k_gj_update(double* __restrict__ A, int n, int p0, int b,
+                            const double* __restrict__ Pinv, const double* __restrict__ U,
+                            const double* __restrict__ Lo) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= (int64_t)n * n) return;
   const int r = (int)(q / n), c = (int)(q % n);
-  // one division per thread (a float64 division is a long instruction
-  // sequence on the double pipe); the others multiply by the reciprocal
-  const double ip = 1.0 / A[(int64_t)p * n + p];
+  const bool rp = r >= p0 && r < p0 + b, cp = c >= p0 && c < p0 + b;
   double v;
-  if (r == p && c == p) v = ip;
-  else if (r == p) v = A[(int64_t)p * n + c] * ip;
-  else if (c == p) v = -A[(int64_t)r * n + p] * ip;
-  else v = A[q] - A[(int64_t)r * n + p] * (A[(int64_t)p * n + c] * ip);
-  B[q] = v;
+  if (rp && cp) {
+    v = Pinv[(r - p0) * kGjB + (c - p0)];
+  } else if (rp) {
+    v = U[(int64_t)(r - p0) * n + c];
+  } else if (cp) {
+    v = 0.0;  // -A_OP A_PP^-1
+    for (int u = 0; u < b; ++u) v -= Lo[(int64_t)r * kGjB + u] * Pinv[u * kGjB + (c - p0)];
+  } else {
+    v = A[q];
+    for (int u = 0; u < b; ++u) v -= Lo[(int64_t)r * kGjB + u] * U[(int64_t)u * n + c];
+  }
+  A[q] = v;
 }
 
 constexpr int kRowsPerBlock = 8;
@@ -83,14 +137,19 @@ cudaError_t launch_dense_gather(const Grid& g, const double* C, const int* cfree
 }
 
 cudaError_t launch_dense_invert(double* A, double* B, int n, double** result, cudaStream_t st) {
-  int64_t nn = (int64_t)n * n;
-  int blocks = (int)((nn + 255) / 256);
-  double *src = A, *dst = B;
-  for (int p = 0; p < n; ++p) {
-    k_gj_step<<<blocks, 256, 0, st>>>(src, dst, n, p); count_launches(1);
-    double* t = src; src = dst; dst = t;
+  // B holds the step's small buffers: pivot inverse, then U (b x n), then Lo (n x b)
+  double* Pinv = B;
+  double* U = B + kGjB * kGjB;
+  double* Lo = U + (int64_t)kGjB * n;
+  const int64_t nn = (int64_t)n * n;
+  for (int p0 = 0; p0 < n; p0 += kGjB) {
+    const int b = n - p0 < kGjB ? n - p0 : kGjB;
+    k_gj_pivot<<<1, 256, 0, st>>>(A, n, p0, b, Pinv);
+    k_gj_panel<<<(int)(((int64_t)b * n + 255) / 256), 256, 0, st>>>(A, n, p0, b, Pinv, U, Lo);
+    k_gj_update<<<(int)((nn + 255) / 256), 256, 0, st>>>(A, n, p0, b, Pinv, U, Lo);
+    count_launches(3);
   }
-  *result = src;
+  *result = A;
   return cudaGetLastError();
 }
 

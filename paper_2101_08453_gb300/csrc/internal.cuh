@@ -84,6 +84,13 @@ __host__ __device__ inline bool is_free(const Grid& g, int i, int j, int k) {
 // their two coarse neighbours (Sec. 3, the weights of trilinear
 // interpolation on a regular grid).  Vertical: kf[K] = fine layer of coarse
 // layer K (non-uniform after per-layer semicoarsening).
+// V-cycles between two float64 convergence checks: the option, or its
+// default (6 in mixed precision, 1 in float64)
+inline int effective_cycles_per_check(const mcwind_options& o) {
+  if (o.cycles_per_check > 0) return o.cycles_per_check;
+  return o.precision == MCWIND_PREC_MIXED ? 6 : 1;
+}
+
 struct Transfer {
   int hx, hy;
   int Nzf, Nzc;

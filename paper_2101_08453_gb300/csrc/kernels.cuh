@@ -30,6 +30,13 @@ cudaError_t launch_recover(const Grid& g, int nx, int ny, int nz, const double* 
                            double* u, cudaStream_t st);
 // recovery at the element centers in float pairs (xyz2, u2, lam2 pre-split in
 // the [k][j][i] layout; u0c != nullptr: u0 given at the centers instead of u2)
+// u at the element centers of a shift-form grid (Eq. 3) from the column's
+// center Jacobian and each layer's thickness, in float pairs; u0 nodal
+// [3][N] or, with u0 = nullptr, u0c at the centers [3][NE]
+cudaError_t launch_recover_center_sep(int nx, int ny, int nz, const double* X, const double* Y,
+                                      const double* Z, const double* u0, const double* u0c,
+                                      const double* lam, const double* a, double* u,
+                                      cudaStream_t st);
 cudaError_t launch_recover_center_df(int nx, int ny, int nz, const float2* xyz2, const float2* u2,
                                      const double* u0c, const float2* lam2, const double* a,
                                      double* u, cudaStream_t st);
@@ -142,8 +149,9 @@ cudaError_t launch_shift_check(int Nx, int Ny, int Nz, const double* X, const do
                                const double* Z, int* flag, cudaStream_t st);
 // finest horizontal factors from the ground layer of X, Y, Z (standard
 // layout), fixed couplings zeroed, float32 tiles written; flag |= 1 on j2 <= 0
+// pairs: the cell sums in float pairs (else float64)
 cudaError_t launch_hfactors(const Grid& g, const double* X, const double* Y, const double* Z,
-                            const double* a, double* H64, float* H32, int* flag,
+                            const double* a, double* H64, float* H32, int* flag, bool pairs,
                             cudaStream_t st);
 cudaError_t launch_hfactor_finalize(const Grid& g, double* H64, float* H32, cudaStream_t st);
 // one direction (0: x, 1: y) of Ph^T H Ph for the 4 terms (float64)
@@ -162,9 +170,10 @@ cudaError_t launch_rhs_sep(const Level& L, const float2* R2, const float2* VR2, 
                            float2* u2, double* f, int* status, cudaStream_t st);
 cudaError_t launch_vgalerkin(const Transfer& tr, const double* Vf, double* Vc, float* Vc32,
                              cudaStream_t st);
-// 27-point rows from float64 factors into a tiled float64 operator (planes 0..26)
+// 27-point rows from float64 factors into a tiled float64 operator, planes
+// 0..26 and 27 = 1/diag (flag |= 2 on a free diagonal that is not positive)
 cudaError_t launch_sep_expand64(const Grid& g, const double* H64, const double* V64, double* C,
-                                cudaStream_t st);
+                                int* flag, bool pairs, cudaStream_t st);
 // rows from the factors in the standard layout [27][N] (T = double: float64
 // planes; T = float: float32 tiles)
 template <typename T>

@@ -229,7 +229,8 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
     off = align256(off + p->tmp_bytes + kPlanes * tmpB * 8);
   }
   p->n_coarse = (int)nc;
-  p->off_dense = off; off = align256(off + 2 * (size_t)nc * nc * 8);
+  // the inverse, then the blocked Gauss-Jordan's panels (16 x 16 + 2 x 16 n)
+  p->off_dense = off; off = align256(off + ((size_t)nc * nc + 256 + 32 * (size_t)nc) * 8);
   p->off_cfree = off; off = align256(off + (size_t)nc * 4);
   if (o.accel == MCWIND_ACCEL_CG) {
     const size_t t0 = (size_t)p->lv[0].g.total;
@@ -257,7 +258,10 @@ extern "C" int mcwind_plan_create(int nx, int ny, int nz, const double a[3], dou
 
 extern "C" int mcwind_plan_query(mcwind_plan p, mcwind_options* opt, size_t* workspace_bytes) {
   if (!p) return MCWIND_EINVAL;
-  if (opt) *opt = p->opt;
+  if (opt) {
+    *opt = p->opt;
+    opt->cycles_per_check = effective_cycles_per_check(p->opt);
+  }
   if (workspace_bytes) *workspace_bytes = p->ws_bytes;
   return MCWIND_OK;
 }

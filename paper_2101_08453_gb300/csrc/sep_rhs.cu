@@ -11,12 +11,13 @@
 // element, (h/2) m and int psi_a' psi_b (the transpose of g):
 //   f = -[(E_x (x) V_M) u_x + (E_y (x) V_M) u_y - (F_x (x) V_G^T) u_x
 //         - (F_y (x) V_G^T) u_y + (M_z (x) V_G^T) u_z].
-// The factors are formed in float64 and kept as float pairs; the load
-// vector is summed in float pairs (about 48 significant bits), as the
-// element kernels of this arithmetic do.
+// The factors are formed and kept as float pairs, and the load vector is
+// summed in float pairs (about 48 significant bits), as the element kernels
+// of this arithmetic do.
 #include <cudaTypedefs.h>
 
 #include "async.cuh"
+#include "cellgeom.cuh"
 #include "dfloat.cuh"
 #include "kernels.cuh"
 
@@ -56,10 +57,13 @@ __device__ __forceinline__ float2 pnorm(float sh, float sl) {
 
 // Factors of the cells of one parity class added, as float pairs, into the
 // tiles of their 4 corner columns (classes in order: fixed summation order).
+// The Gauss sums run in float pairs from the cell's edge vectors; F_x, F_y
+// and M_z are symmetric in (p, q), so their upper triangles are formed.
 __global__ void __launch_bounds__(128) k_rhs_cells(Grid g, int cls, const double* __restrict__ X,
                                                    const double* __restrict__ Y,
                                                    const double* __restrict__ Z,
                                                    float2* __restrict__ R) {
+  using A = Arith<dflt>;
   const int ci = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + (cls & 1);
   const int cj = 2 * (blockIdx.y * blockDim.y + threadIdx.y) + (cls >> 1);
   if (ci >= g.Nx - 1 || cj >= g.Ny - 1) return;
@@ -69,43 +73,36 @@ __global__ void __launch_bounds__(128) k_rhs_cells(Grid g, int cls, const double
     const int64_t n = (int64_t)(cj + (p >> 1)) * g.Nx + ci + (p & 1);
     xs[p] = X[n]; ys[p] = Y[n]; zs[p] = Z[n];
   }
-  double Ex[4][4], Ey[4][4], Fx[4][4], Fy[4][4], Mz[4][4];
+  const CellEdges<dflt> ce = cell_edges<dflt>(xs, ys, zs);
+  dflt Ex[4][4], Ey[4][4], Fx[10], Fy[10], Mz[10];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Ex[p][q] = Ey[p][q] = Fx[p][q] = Fy[p][q] = Mz[p][q] = 0.0;
-  const double gp = 0.57735026918962576451;  // 1/sqrt(3)
+    for (int q = 0; q < 4; ++q) Ex[p][q] = Ey[p][q] = A::zero();
+#pragma unroll
+  for (int u = 0; u < 10; ++u) Fx[u] = Fy[u] = Mz[u] = A::zero();
 #pragma unroll
   for (int gq = 0; gq < 4; ++gq) {
-    const double e1 = (gq & 1) ? gp : -gp, e2 = (gq & 2) ? gp : -gp;
-    double phi[4], d1[4], d2[4];
+    const GaussGeom<dflt> G = gauss_geom(ce, gq);
+    const dflt j2 = G.J00 * G.J11 - G.J01 * G.J10;
+    const dflt zx = G.J11 * G.z1 - G.J10 * G.z2, zy = G.J00 * G.z2 - G.J01 * G.z1;  // adj^T z'
+    int t = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const double sx = (p & 1) ? 1.0 : -1.0, sy = (p & 2) ? 1.0 : -1.0;
-      phi[p] = 0.25 * (1.0 + sx * e1) * (1.0 + sy * e2);
-      d1[p] = 0.25 * sx * (1.0 + sy * e2);
-      d2[p] = 0.25 * sy * (1.0 + sx * e1);
-    }
-    double J00 = 0, J01 = 0, J10 = 0, J11 = 0, z1 = 0, z2 = 0;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      J00 += xs[p] * d1[p]; J01 += xs[p] * d2[p];
-      J10 += ys[p] * d1[p]; J11 += ys[p] * d2[p];
-      z1 += zs[p] * d1[p]; z2 += zs[p] * d2[p];
-    }
-    const double j2 = J00 * J11 - J01 * J10;
-    const double zx = J11 * z1 - J10 * z2, zy = -J01 * z1 + J00 * z2;  // adj^T z'
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const double gx = J11 * d1[p] - J10 * d2[p], gy = -J01 * d1[p] + J00 * d2[p];
+      const dflt d1 = A::from(gauss_d1(gq, p)), d2 = A::from(gauss_d2(gq, p));
+      const dflt gx = G.J11 * d1 - G.J10 * d2, gy = G.J00 * d2 - G.J01 * d1;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const double pp = phi[p] * phi[q];
-        Ex[p][q] += gx * phi[q];
-        Ey[p][q] += gy * phi[q];
-        Fx[p][q] += zx * pp;
-        Fy[p][q] += zy * pp;
-        Mz[p][q] += j2 * pp;
+        const dflt phq = A::from(gauss_phi(gq, q));
+        Ex[p][q] = Ex[p][q] + gx * phq;
+        Ey[p][q] = Ey[p][q] + gy * phq;
+        if (q >= p) {
+          const dflt pp = A::from(gauss_phi(gq, p) * gauss_phi(gq, q));
+          Fx[t] = Fx[t] + zx * pp;
+          Fy[t] = Fy[t] + zy * pp;
+          Mz[t] = Mz[t] + j2 * pp;
+          ++t;
+        }
       }
     }
   }
@@ -115,11 +112,13 @@ __global__ void __launch_bounds__(128) k_rhs_cells(Grid g, int cls, const double
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int s2 = ((q & 1) - (p & 1) + 1) + 3 * ((q >> 1) - (p >> 1) + 1);
-      const double v[5] = {Ex[p][q], Ey[p][q], Fx[p][q], Fy[p][q], Mz[p][q]};
+      const int lo = p < q ? p : q, hi = p < q ? q : p;
+      const int t = lo * 4 - lo * (lo - 1) / 2 + (hi - lo);  // upper-triangle index
+      const dflt v[5] = {Ex[p][q], Ey[p][q], Fx[t], Fy[t], Mz[t]};
 #pragma unroll
-      for (int t = 0; t < 5; ++t) {
-        float2& r = R[ridx(col, 9 * t + s2)];
-        r = pair_add(r, split_bits(v[t]));
+      for (int c = 0; c < 5; ++c) {
+        float2& r = R[ridx(col, 9 * c + s2)];
+        r = pair_add(r, make_float2(v[c].hi, v[c].lo));
       }
     }
   }

@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include "async.cuh"
+#include "cellgeom.cuh"
 #include "dfloat.cuh"
 #include "kernels.cuh"
 
@@ -35,26 +36,59 @@ __device__ __forceinline__ bool free_column(const Grid& g, int i, int j) {
   return i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2;
 }
 
+// acc += a * b in float pairs: the product's rounding error kept by the FMA,
+// the sum's by a two-sum; the low part is renormalized by the caller
+__device__ __forceinline__ void pmac2(float& sh, float& sl, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = sh + p;
+  const float bb = s - sh;
+  const float t = (sh - (s - bb)) + (p - bb);
+  sh = s;
+  sl += t + e;
+}
+
 // ---------------------------------------------------------------- set-up
 
 // flag |= 8 unless X and Y do not depend on k and Z(i,j,k) - Z(i,j,0) equals
-// Z(0,0,k) - Z(0,0,0), to 1e-10 of the coordinates' magnitude (the
-// generator's rounding of z_s + zeta is far below it).  Standard layout.
+// zeta_k = Z(0,0,k) - Z(0,0,0), each to about 1e-10 of the largest
+// coordinate magnitude involved (the generator's rounding of z_s + zeta is
+// far below it).  Standard layout.  One thread per node above the ground
+// layer (blockIdx.z = k - 1); equal X and Y are recognised by their bits,
+// and "small" is decided on the exponents: |d| < 2^-33 max (one float64
+// subtraction per node besides the two of the z test, which matters at the
+// float64 issue rate).
+__device__ __forceinline__ long long mag_bits(double v) {
+  return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL;
+}
+
 __global__ void k_shift_check(int Nx, int Ny, int Nz, const double* __restrict__ X,
                               const double* __restrict__ Y, const double* __restrict__ Z,
                               int* flag) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= Nx || j >= Ny) return;
+  __shared__ double zeta;
+  __shared__ long long mlay;
+  const int k = (int)blockIdx.z + 1;
   const int64_t lay = (int64_t)Nx * Ny;
-  const int64_t c = (int64_t)j * Nx + i;
-  const double x0 = X[c], y0 = Y[c], z0 = Z[c], zb = Z[0];
-  bool ok = true;
-  for (int k = 1; k < Nz; ++k) {
-    const double xk = X[k * lay + c], yk = Y[k * lay + c], zk = Z[k * lay + c], zr = Z[k * lay];
-    const double tol = 1e-10 * (fabs(x0) + fabs(y0) + fabs(zk) + fabs(z0) + fabs(zr) + fabs(zb));
-    ok = ok && fabs(xk - x0) <= tol && fabs(yk - y0) <= tol && fabs((zk - z0) - (zr - zb)) <= tol;
+  if (threadIdx.x == 0) {
+    const double zr = Z[k * lay], zb = Z[0];
+    zeta = zr - zb;
+    mlay = max(mag_bits(zr), mag_bits(zb));
   }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= Nx || j >= Ny || k >= Nz) return;
+  const int64_t c = (int64_t)j * Nx + i;
+  const double x0 = X[c], y0 = Y[c], z0 = Z[c];
+  const double xk = X[k * lay + c], yk = Y[k * lay + c], zk = Z[k * lay + c];
+  const long long m = max(max(mag_bits(x0), mag_bits(y0)), max(max(mag_bits(z0), mag_bits(zk)), mlay));
+  const int lim = (int)(m >> 52) - 34;  // biased exponent bound of a small difference
+  auto small = [lim](double d) { return (int)(mag_bits(d) >> 52) <= lim; };
+  bool ok = small((zk - z0) - zeta);
+  if (__double_as_longlong(xk) != __double_as_longlong(x0)) ok = ok && small(xk - x0);
+  if (__double_as_longlong(yk) != __double_as_longlong(y0)) ok = ok && small(yk - y0);
   if (!ok) atomicOr(flag, kShiftFlag);
 }
 
@@ -62,13 +96,16 @@ __global__ void k_shift_check(int Nx, int Ny, int Nz, const double* __restrict__
 // ci & 1 = cls & 1, cj & 1 = cls >> 1), added into the float64 planes of
 // their 4 corner columns: cells of one class share no corner, and the four
 // classes run in order, so every sum is formed in one fixed order.  2 x 2
-// Gauss points in (xi1, xi2), float64.  Corner p = a + 2b is node
-// (ci + a, cj + b) of the ground layer (standard layout).
+// Gauss points in (xi1, xi2), in arithmetic R (float64 or float pairs).
+// Corner p = a + 2b is node (ci + a, cj + b) of the ground layer (standard
+// layout).  P and R are symmetric, so only their upper triangles are formed.
+template <typename R>
 __global__ void __launch_bounds__(128) k_hfactor_cells(Grid g, int cls, const double* __restrict__ X,
                                                        const double* __restrict__ Y,
-                                                       const double* __restrict__ Z, double c1,
-                                                       double c2, double c3,
+                                                       const double* __restrict__ Z, double c1d,
+                                                       double c2d, double c3d,
                                                        double* __restrict__ H, int* flag) {
+  using A = Arith<R>;
   const int ci = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + (cls & 1);
   const int cj = 2 * (blockIdx.y * blockDim.y + threadIdx.y) + (cls >> 1);
   if (ci >= g.Nx - 1 || cj >= g.Ny - 1) return;
@@ -78,55 +115,50 @@ __global__ void __launch_bounds__(128) k_hfactor_cells(Grid g, int cls, const do
     const int64_t n = (int64_t)(cj + (p >> 1)) * g.Nx + ci + (p & 1);
     xs[p] = X[n]; ys[p] = Y[n]; zs[p] = Z[n];
   }
-  double P[4][4], Q[4][4], R[4][4];
+  const CellEdges<R> ce = cell_edges<R>(xs, ys, zs);
+  const R c1 = A::from(c1d), c2 = A::from(c2d), c3 = A::from(c3d);
+  R P[10], Q[4][4], Rr[10];  // P, R: upper triangles, index tri(p, q)
+#pragma unroll
+  for (int u = 0; u < 10; ++u) P[u] = Rr[u] = A::zero();
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) P[p][q] = Q[p][q] = R[p][q] = 0.0;
-  const double gp = 0.57735026918962576451;  // 1/sqrt(3)
+    for (int q = 0; q < 4; ++q) Q[p][q] = A::zero();
   bool bad = false;
 #pragma unroll
   for (int gq = 0; gq < 4; ++gq) {
-    const double e1 = (gq & 1) ? gp : -gp, e2 = (gq & 2) ? gp : -gp;
-    double phi[4], d1[4], d2[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const double sx = (p & 1) ? 1.0 : -1.0, sy = (p & 2) ? 1.0 : -1.0;
-      phi[p] = 0.25 * (1.0 + sx * e1) * (1.0 + sy * e2);
-      d1[p] = 0.25 * sx * (1.0 + sy * e2);
-      d2[p] = 0.25 * sy * (1.0 + sx * e1);
-    }
-    double J00 = 0, J01 = 0, J10 = 0, J11 = 0, z1 = 0, z2 = 0;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      J00 += xs[p] * d1[p]; J01 += xs[p] * d2[p];
-      J10 += ys[p] * d1[p]; J11 += ys[p] * d2[p];
-      z1 += zs[p] * d1[p]; z2 += zs[p] * d2[p];
-    }
-    const double j2 = J00 * J11 - J01 * J10;
-    bad = bad || !(j2 > 0.0);
-    const double ij = 1.0 / j2;
+    const GaussGeom<R> G = gauss_geom(ce, gq);
+    const R j2 = G.J00 * G.J11 - G.J01 * G.J10;
+    bad = bad || !A::pos(j2);
+    const R ij = A::rcp(j2);
     // W = adj D adj^T / j2 with adj = [[J11, -J01], [-J10, J00]]
-    const double W00 = (c1 * J11 * J11 + c2 * J01 * J01) * ij;
-    const double W01 = -(c1 * J11 * J10 + c2 * J01 * J00) * ij;
-    const double W11 = (c1 * J10 * J10 + c2 * J00 * J00) * ij;
-    const double v1 = W00 * z1 + W01 * z2, v2 = W01 * z1 + W11 * z2;  // W z'
-    const double s = z1 * v1 + z2 * v2 + c3 * j2;
-    double wg1[4], wg2[4], u[4];
+    const R W00 = (c1 * (G.J11 * G.J11) + c2 * (G.J01 * G.J01)) * ij;
+    const R W01 = -((c1 * (G.J11 * G.J10) + c2 * (G.J01 * G.J00)) * ij);
+    const R W11 = (c1 * (G.J10 * G.J10) + c2 * (G.J00 * G.J00)) * ij;
+    const R v1 = W00 * G.z1 + W01 * G.z2, v2 = W01 * G.z1 + W11 * G.z2;  // W z'
+    const R s = G.z1 * v1 + G.z2 * v2 + c3 * j2;
+    R wg1[4], wg2[4], u[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      wg1[p] = W00 * d1[p] + W01 * d2[p];
-      wg2[p] = W01 * d1[p] + W11 * d2[p];
-      u[p] = d1[p] * v1 + d2[p] * v2;
+      const R d1 = A::from(gauss_d1(gq, p)), d2 = A::from(gauss_d2(gq, p));
+      wg1[p] = W00 * d1 + W01 * d2;
+      wg2[p] = W01 * d1 + W11 * d2;
+      u[p] = d1 * v1 + d2 * v2;
     }
+    int t = 0;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 4; ++p) {
+      const R d1 = A::from(gauss_d1(gq, p)), d2 = A::from(gauss_d2(gq, p));
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        P[p][q] += d1[p] * wg1[q] + d2[p] * wg2[q];
-        Q[p][q] += u[p] * phi[q];
-        R[p][q] += s * phi[p] * phi[q];
+        Q[p][q] = Q[p][q] + u[p] * A::from(gauss_phi(gq, q));
+        if (q >= p) {
+          P[t] = P[t] + (d1 * wg1[q] + d2 * wg2[q]);
+          Rr[t] = Rr[t] + s * A::from(gauss_phi(gq, p) * gauss_phi(gq, q));
+          ++t;
+        }
       }
+    }
   }
   if (bad) atomicOr(flag, 1);
 #pragma unroll
@@ -135,10 +167,12 @@ __global__ void __launch_bounds__(128) k_hfactor_cells(Grid g, int cls, const do
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int s2 = ((q & 1) - (p & 1) + 1) + 3 * ((q >> 1) - (p >> 1) + 1);
-      H[(0 * 9 + s2) * g.PP + col] += P[p][q];
-      H[(1 * 9 + s2) * g.PP + col] -= Q[p][q];
-      H[(2 * 9 + s2) * g.PP + col] -= Q[q][p];
-      H[(3 * 9 + s2) * g.PP + col] += R[p][q];
+      const int lo = p < q ? p : q, hi = p < q ? q : p;
+      const int t = lo * 4 - lo * (lo - 1) / 2 + (hi - lo);  // tri(lo, hi)
+      H[(0 * 9 + s2) * g.PP + col] += A::to_double(P[t]);
+      H[(1 * 9 + s2) * g.PP + col] -= A::to_double(Q[p][q]);
+      H[(2 * 9 + s2) * g.PP + col] -= A::to_double(Q[q][p]);
+      H[(3 * 9 + s2) * g.PP + col] += A::to_double(Rr[t]);
     }
   }
 }
@@ -203,7 +237,10 @@ __device__ __forceinline__ float sep32_coef(const float hq[4], const float* v, i
 // Ph^T H_t Ph, for all four terms: out(I; D, e) = sum_a w_a sum_d
 // H(f_I + a; d, e) P(f_I + a + d, I + D) with the interpolation weights of
 // Sec. 3 (a, d, D in {-1, 0, 1}; e the offset in the other direction).  One
-// thread per output column, float64; inputs outside the grid have weight 0.
+// thread per output column; inputs outside the grid have weight 0.  The
+// weights are 0, 1/2 and 1, so every product w_a P v is exact; the sums run
+// in float pairs (about 48 significant bits, FP32 pipe) and each output is
+// rounded to float64 once.
 template <int DIM>
 __global__ void __launch_bounds__(128) k_hgalerkin(Grid gin, Grid gout,
                                                    const double* __restrict__ Hin,
@@ -215,45 +252,48 @@ __global__ void __launch_bounds__(128) k_hgalerkin(Grid gin, Grid gout,
   const int Nf = DIM == 0 ? gin.Nx : gin.Ny;
   const int Nc = DIM == 0 ? gout.Nx : gout.Ny;
   int f;
-  double wa[3];
+  float wa[3];
   hcoarse(1, Nf, Nc, Iout, f, wa[0], wa[2]);
-  wa[1] = 1.0;
-  double Pw[5][3];  // Pw[q][D] = P(f + q - 2, Iout + D - 1)
+  wa[1] = 1.0f;
+  float Pw[5][3];  // Pw[q][D] = P(f + q - 2, Iout + D - 1)
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const int b = f + q - 2;
     int c0 = -100, c1 = -100;
-    double w0 = 0.0, w1 = 0.0;
+    float w0 = 0.0f, w1 = 0.0f;
     if (b >= 0 && b <= Nf - 1) hpair(1, Nf, Nc, b, c0, w0, c1, w1);
 #pragma unroll
     for (int D = 0; D < 3; ++D) {
       const int J = Iout + D - 1;
-      Pw[q][D] = (c0 == J ? w0 : 0.0) + (c1 == J && c1 != c0 ? w1 : 0.0);
+      Pw[q][D] = (c0 == J ? w0 : 0.0f) + (c1 == J && c1 != c0 ? w1 : 0.0f);
     }
   }
   const int64_t o = gidx(gout, i, j, 0);
   for (int t = 0; t < 4; ++t) {
-    double acc[9];
+    dflt acc[9];
 #pragma unroll
-    for (int s = 0; s < 9; ++s) acc[s] = 0.0;
+    for (int s = 0; s < 9; ++s) acc[s] = dflt{0.0f, 0.0f};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      if (wa[a] == 0.0) continue;
+      if (wa[a] == 0.0f) continue;
       const int ii = DIM == 0 ? f + a - 1 : i, jj = DIM == 1 ? f + a - 1 : j;
       const int64_t in = gidx(gin, ii, jj, 0);
 #pragma unroll
       for (int s = 0; s < 9; ++s) {
         const int d = DIM == 0 ? s % 3 : s / 3, e = DIM == 0 ? s / 3 : s % 3;
-        const double v = wa[a] * Hin[(t * 9 + s) * gin.PP + in];
+        const float2 v2 = split_bits(Hin[(t * 9 + s) * gin.PP + in]);
 #pragma unroll
         for (int D = 0; D < 3; ++D) {
-          const double w = Pw[a + d][D];
-          if (w != 0.0) acc[DIM == 0 ? D + 3 * e : e + 3 * D] += v * w;
+          const float w = wa[a] * Pw[a + d][D];  // 0, 1/4, 1/2 or 1: exact
+          if (w != 0.0f) {
+            dflt& r = acc[DIM == 0 ? D + 3 * e : e + 3 * D];
+            r = r + dflt{v2.x * w, v2.y * w};
+          }
         }
       }
     }
 #pragma unroll
-    for (int s = 0; s < 9; ++s) Hout[(t * 9 + s) * gout.PP + o] = acc[s];
+    for (int s = 0; s < 9; ++s) Hout[(t * 9 + s) * gout.PP + o] = pair_to_double(acc[s].hi, acc[s].lo);
   }
 }
 
@@ -337,40 +377,101 @@ __global__ void k_vgalerkin(Transfer tr, const double* __restrict__ Vf, double* 
 }
 
 // Expanded 27-point rows from float64 factors into the tiled float64
-// operator (planes 0..26; plane 27 is set by the stencil finalization), in
-// the three-term form: coefficient (s2, dk) = P V_M + R V_K + S A (+ T B on
-// the ground layer's diagonal), S = H_Q - H_Q^T, T = H_Q + H_Q^T,
-// A = (V_G - V_G^T)/2, B = (V_G + V_G^T)/2.  The entries of V_G are dyadic
-// and so are the interpolation weights, so B is exactly -1/2 at (0, 0) and 0
-// elsewhere and A(k, k) is exactly 0: 72 products per node instead of 108.
-// One thread per column (blockIdx.z = parity), walking the layers.
-__global__ void __launch_bounds__(128) k_sep_expand64(Grid g, const double* __restrict__ H,
-                                                      const double* __restrict__ V,
-                                                      double* __restrict__ C) {
+// operator, planes 0..26, and plane 27 = 1/K_nn (0 at fixed nodes; flag |= 2
+// if a free diagonal is not positive).  The factors already zero every
+// coupling that touches a fixed node, so no further masking is needed.
+// Three-term form: coefficient (s2, dk) = P V_M + R V_K + S A (+ T B on the
+// ground layer's diagonal), S = H_Q - H_Q^T, T = H_Q + H_Q^T,
+// A = (V_G - V_G^T)/2, B = (V_G + V_G^T)/2 (B is exactly -1/2 at (0, 0) and 0
+// elsewhere, A(k, k) exactly 0).  PAIRS: the products and sums run in float
+// pairs (about 48 significant bits, FP32 pipe; each coefficient is rounded
+// to float64 once); otherwise in float64, as sum_t H_t V_t over the four
+// terms.  The reciprocal of the diagonal is float64.  One thread per column
+// (blockIdx.z = parity), walking the layers; the block first turns the
+// level's vertical factors into float pairs in shared memory.
+template <bool PAIRS>
+__global__ void __launch_bounds__(128) k_sep_expand(Grid g, const double* __restrict__ H,
+                                                    const double* __restrict__ V,
+                                                    double* __restrict__ C, int* flag) {
+  if (!PAIRS) {
+    const int hh = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int par = blockIdx.z;
+    if (hh >= g.H || j >= g.Ny) return;
+    const int i = 2 * hh + par;
+    const int64_t col = (int64_t)j * g.RP + (int64_t)par * g.H + hh;
+    const bool fcol = i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2;
+    for (int k = 0; k < g.Nz; ++k) {
+      const int64_t b = (int64_t)k * g.PP + col;
+      double diag = 0.0;
+#pragma unroll
+      for (int s = 0; s < 27; ++s) {
+        const int s2 = s % 9, dk = s / 9;
+        double c = 0.0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) c += H[(t * 9 + s2) * g.PP + col] * V[k * kVF + 3 * t + dk];
+        C[cidx(b, s)] = c;
+        if (s == 13) diag = c;
+      }
+      const bool fr = fcol && k <= g.Nz - 2;
+      if (fr && !(diag > 0.0)) atomicOr(flag, 2);
+      C[cidx(b, kInvDiag)] = fr ? 1.0 / diag : 0.0;
+    }
+    return;
+  }
+  __shared__ float2 vs[kMaxZ][9];  // M(3), K(3), A(k,k-1), A(k,k+1), B(k,k)
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int q = tid; q < g.Nz * 9; q += blockDim.x * blockDim.y) {
+    const int k = q / 9, e = q % 9;
+    const double* v = V + k * kVF;
+    double x;
+    if (e < 3) x = v[e];
+    else if (e < 6) x = v[9 + e - 3];
+    else if (e == 6) x = 0.5 * (v[3] - v[6]);
+    else if (e == 7) x = 0.5 * (v[5] - v[8]);
+    else x = 0.5 * (v[4] + v[7]);
+    vs[k][e] = split_bits(x);
+  }
+  __syncthreads();
   const int hh = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int par = blockIdx.z;
   if (hh >= g.H || j >= g.Ny) return;
+  const int i = 2 * hh + par;
   const int64_t col = (int64_t)j * g.RP + (int64_t)par * g.H + hh;
-  double P[9], S[9], T[9], R[9];
+  float2 P[9], S[9], T[9], R[9];
 #pragma unroll
   for (int s2 = 0; s2 < 9; ++s2) {
     const double q = H[(9 + s2) * g.PP + col], qt = H[(18 + s2) * g.PP + col];
-    P[s2] = H[s2 * g.PP + col];
-    S[s2] = q - qt;
-    T[s2] = q + qt;
-    R[s2] = H[(27 + s2) * g.PP + col];
+    P[s2] = split_bits(H[s2 * g.PP + col]);
+    S[s2] = split_bits(q - qt);
+    T[s2] = split_bits(q + qt);
+    R[s2] = split_bits(H[(27 + s2) * g.PP + col]);
   }
+  const bool fcol = i >= 1 && i <= g.Nx - 2 && j >= 1 && j <= g.Ny - 2;
   for (int k = 0; k < g.Nz; ++k) {
-    const double* v = V + k * kVF;
-    const double Ab = 0.5 * (v[3] - v[6]), Aa = 0.5 * (v[5] - v[8]), Bc = 0.5 * (v[4] + v[7]);
+    const float2* v = vs[k];
     const int64_t b = (int64_t)k * g.PP + col;
+    double diag = 0.0;
 #pragma unroll
     for (int s2 = 0; s2 < 9; ++s2) {
-      C[cidx(b, s2)] = fma(S[s2], Ab, fma(P[s2], v[0], R[s2] * v[9]));
-      C[cidx(b, 9 + s2)] = fma(T[s2], Bc, fma(P[s2], v[1], R[s2] * v[10]));
-      C[cidx(b, 18 + s2)] = fma(S[s2], Aa, fma(P[s2], v[2], R[s2] * v[11]));
+#pragma unroll
+      for (int dk = 0; dk < 3; ++dk) {
+        float sh = 0.0f, sl = 0.0f;
+        pmac2(sh, sl, P[s2], v[dk]);
+        pmac2(sh, sl, R[s2], v[3 + dk]);
+        if (dk == 0) pmac2(sh, sl, S[s2], v[6]);
+        if (dk == 2) pmac2(sh, sl, S[s2], v[7]);
+        if (dk == 1 && k == 0) pmac2(sh, sl, T[s2], v[8]);
+        const float hi = sh + sl, lo = sl - (hi - sh);
+        const double c = pair_to_double(hi, lo);
+        C[cidx(b, dk * 9 + s2)] = c;
+        if (dk == 1 && s2 == 4) diag = c;
+      }
     }
+    const bool fr = fcol && k <= g.Nz - 2;
+    if (fr && !(diag > 0.0)) atomicOr(flag, 2);
+    C[cidx(b, kInvDiag)] = fr ? 1.0 / diag : 0.0;
   }
 }
 
@@ -744,21 +845,25 @@ __global__ void __launch_bounds__(32 * (kGsR + 1)) k_residual_sep_staged(
 
 cudaError_t launch_shift_check(int Nx, int Ny, int Nz, const double* X, const double* Y,
                                const double* Z, int* flag, cudaStream_t st) {
-  k_shift_check<<<dim3((Nx + 31) / 32, (Ny + 3) / 4), dim3(32, 4), 0, st>>>(Nx, Ny, Nz, X, Y, Z,
-                                                                          flag);
+  if (Nz < 2) return cudaSuccess;
+  k_shift_check<<<dim3((Nx + 255) / 256, Ny, Nz - 1), dim3(256, 1), 0, st>>>(Nx, Ny, Nz, X, Y, Z,
+                                                                           flag);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_hfactors(const Grid& g, const double* X, const double* Y, const double* Z,
-                            const double* a, double* H64, float* H32, int* flag,
+                            const double* a, double* H64, float* H32, int* flag, bool pairs,
                             cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(H64, 0, sizeof(double) * kHF * (size_t)g.PP, st);
   const double c1 = 1.0 / (a[0] * a[0]), c2 = 1.0 / (a[1] * a[1]), c3 = 1.0 / (a[2] * a[2]);
   // cells (Nx - 1) x (Ny - 1), a quarter of them per class
   const dim3 grd((g.Nx / 2 + 31) / 32, (g.Ny / 2 + 3) / 4);
   for (int cls = 0; cls < 4 && e == cudaSuccess; ++cls) {
-    k_hfactor_cells<<<grd, dim3(32, 4), 0, st>>>(g, cls, X, Y, Z, c1, c2, c3, H64, flag);
+    if (pairs)
+      k_hfactor_cells<dflt><<<grd, dim3(32, 4), 0, st>>>(g, cls, X, Y, Z, c1, c2, c3, H64, flag);
+    else
+      k_hfactor_cells<double><<<grd, dim3(32, 4), 0, st>>>(g, cls, X, Y, Z, c1, c2, c3, H64, flag);
     count_launches(1);
     e = cudaGetLastError();
   }
@@ -795,8 +900,10 @@ cudaError_t launch_vgalerkin(const Transfer& tr, const double* Vf, double* Vc, f
 }
 
 cudaError_t launch_sep_expand64(const Grid& g, const double* H64, const double* V64, double* C,
-                                cudaStream_t st) {
-  k_sep_expand64<<<dim3((g.H + 31) / 32, (g.Ny + 3) / 4, 2), dim3(32, 4), 0, st>>>(g, H64, V64, C);
+                               int* flag, bool pairs, cudaStream_t st) {
+  const dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
+  if (pairs) k_sep_expand<true><<<grd, dim3(32, 4), 0, st>>>(g, H64, V64, C, flag);
+  else k_sep_expand<false><<<grd, dim3(32, 4), 0, st>>>(g, H64, V64, C, flag);
   count_launches(1);
   return cudaGetLastError();
 }

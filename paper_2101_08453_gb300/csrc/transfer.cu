@@ -27,7 +27,9 @@ __device__ __forceinline__ void block_partial(double s, double* partials) {
 // (the residual of a cycle, before restriction: no norm, no double
 // arithmetic).  MODE 1 (T = double): write (float) r into r32 and zero e32,
 // the start of one float32 correction cycle.  MODE 2: r = K x (f unused) and
-// the partials of x . K x instead of r . r.
+// the partials of x . K x instead of r . r.  MODE 4 / MODE 5: MODE 1 / MODE 0
+// for x = 0 (a cold start), r = f without reading K or x (K 0 = 0 exactly,
+// so the result and its partials are those of the full residual).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __restrict__ C,
                                                           const T* __restrict__ f,
@@ -47,9 +49,20 @@ __global__ void __launch_bounds__(kResThreads) k_residual(Grid g, const T* __res
     if (!fcol) {
       for (int k = 0; k < g.Nz; ++k) {
         const int64_t b = (int64_t)k * PP + own;
-        if (MODE != 1) r[b] = T(0);
+        if (MODE != 1 && MODE != 4) r[b] = T(0);
         else { r32[b] = 0.0f; e32[b] = 0.0f; }
       }
+    } else if (MODE >= 4) {
+      for (int k = 0; k <= g.Nz - 2; ++k) {
+        const int64_t b = (int64_t)k * PP + own;
+        const T acc = f[b];
+        ss += (double)acc * (double)acc;
+        if (MODE == 5) r[b] = acc;
+        else { r32[b] = (float)acc; e32[b] = 0.0f; }
+      }
+      const int64_t b = (int64_t)(g.Nz - 1) * PP + own;
+      if (MODE == 5) r[b] = T(0);
+      else { r32[b] = 0.0f; e32[b] = 0.0f; }
     } else {
       int64_t col[9];
 #pragma unroll
@@ -128,13 +141,21 @@ __device__ __forceinline__ void vcoarse(const Transfer& tr, int K, int& f, W& wm
   wp = (K < tr.Nzc - 1 && tr.kf[K + 1] - tr.kf[K] == 2) ? W(0.5) : W(0);
 }
 
+// a*b + c with one rounding, in the cycle's precision
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return fma(a, b, c); }
+
 // f_c = P^T r (Eq. 7) over one coarse column (I, J), all K: each coarse node
 // gathers up to 3 x 3 x 3 fine residuals with the interpolation weights (1
-// at the coarse node, 1/2 at the half nodes around it), accumulated in the
-// precision of the cycle (T).  HX, HY: the level is coarsened in x, y.
-// Every tap is loaded without a branch (a tap outside the stencil of this
-// node reads a valid neighbour with weight 0, which adds an exact zero), and
-// layers go in chunks of U, so a thread has all loads of U nodes in flight.
+// at the coarse node, 1/2 at the half nodes around it, 0 where a coarse
+// interval spans one fine cell), accumulated in the precision of the cycle
+// (T).  HX, HY: the level is coarsened in x, y.  Per direction the sum is
+// centre + 1/2 (minus + plus), a tap of weight 0 selected to an exact 0, so
+// a coarse node costs two operations per tap and direction instead of a
+// multiply-add per tap of the 27 (on GB300 the float64 pipe, not HBM, bounds
+// the float64 transfers).  Every tap is loaded without a branch (a tap
+// outside the stencil reads a valid neighbour), and layers go in chunks of
+// U, so a thread has all loads of U nodes in flight.
 template <typename T, bool HX, bool HY>
 __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
                                                   const T* __restrict__ r, T* __restrict__ fc) {
@@ -149,36 +170,34 @@ __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
   }
   constexpr int NA = HX ? 3 : 1, NB = HY ? 3 : 1;
   int fi, fj;
-  T ax[3], ay[3];
-  hcoarse(HX ? 1 : 0, gf.Nx, gc.Nx, I, fi, ax[0], ax[2]);
-  hcoarse(HY ? 1 : 0, gf.Ny, gc.Ny, J, fj, ay[0], ay[2]);
-  ax[1] = ay[1] = T(1);
+  float wxm, wxp, wym, wyp;
+  hcoarse(HX ? 1 : 0, gf.Nx, gc.Nx, I, fi, wxm, wxp);
+  hcoarse(HY ? 1 : 0, gf.Ny, gc.Ny, J, fj, wym, wyp);
+  const bool mx = wxm != 0.0f, px = wxp != 0.0f, my = wym != 0.0f, py = wyp != 0.0f;
   // in-layer offsets of the taps (fine columns fi-1..fi+1 are valid: I is interior)
   int64_t hoff[NB][NA];
-  T wx[NA], wy[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
-    wy[b] = HY ? ay[b] : T(1);
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
       const int ii = HX ? fi + a - 1 : fi, jj = HY ? fj + b - 1 : fj;
       hoff[b][a] = (int64_t)jj * gf.RP + (int64_t)(ii & 1) * gf.H + (ii >> 1);
     }
   }
-#pragma unroll
-  for (int a = 0; a < NA; ++a) wx[a] = HX ? ax[a] : T(1);
   const int Kend = gc.Nz - 1;  // the top layer is Dirichlet
   constexpr int U = NA * NB >= 9 ? 1 : (NA * NB >= 3 ? 2 : 4);  // about 12 loads in flight
   for (int K0 = 0; K0 < Kend; K0 += U) {
     T v[U][3][NB][NA];
-    T az[U][3];
+    bool mz[U], pz[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int K = min(K0 + u, Kend - 1);
       int fk;
-      vcoarse(tr, K, fk, az[u][0], az[u][2]);
-      az[u][1] = T(1);
-      const int kl[3] = {az[u][0] != T(0) ? fk - 1 : fk, fk, az[u][2] != T(0) ? fk + 1 : fk};
+      float wzm, wzp;
+      vcoarse(tr, K, fk, wzm, wzp);
+      mz[u] = wzm != 0.0f;
+      pz[u] = wzp != 0.0f;
+      const int kl[3] = {mz[u] ? fk - 1 : fk, fk, pz[u] ? fk + 1 : fk};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const T* rl = r + (int64_t)kl[c] * gf.PP;
@@ -190,25 +209,41 @@ __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      T out = T(0);
+      T col[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c) {
+        T row[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          T row = T(0);
-#pragma unroll
-          for (int a = 0; a < NA; ++a) row += wx[a] * v[u][c][b][a];
-          out += (wy[b] * az[u][c]) * row;
+          if (HX) {
+            const T m = mx ? v[u][c][b][0] : T(0), pl = px ? v[u][c][b][NA - 1] : T(0);
+            row[b] = madd(T(0.5), m + pl, v[u][c][b][NA / 2]);
+          } else {
+            row[b] = v[u][c][b][0];
+          }
         }
+        if (HY) {
+          const T m = my ? row[0] : T(0), pl = py ? row[NB - 1] : T(0);
+          col[c] = madd(T(0.5), m + pl, row[NB / 2]);
+        } else {
+          col[c] = row[0];
+        }
+      }
+      const T m = mz[u] ? col[0] : T(0), pl = pz[u] ? col[2] : T(0);
+      const T out = madd(T(0.5), m + pl, col[1]);
       if (K0 + u < Kend) fc[(int64_t)(K0 + u) * gc.PP + own] = out;
     }
   }
   fc[(int64_t)Kend * gc.PP + own] = T(0);
 }
 
-// x += P e_c (Eq. 7) over one fine column (i, j), all free k: up to 2 x 2 x 2
-// coarse values per node, in precision T; branch-free taps and chunks of U
-// layers as above.
+// x += P e_c (Eq. 7) over one fine column (i, j), all free k.  Per direction
+// a fine node has one coarse tap (weight 1) or two (weight 1/2 each), so its
+// n = 1..8 taps share the weight 2^-m (m = directions with two taps) and
+// x + 2^-m (sum of the taps) costs n - 1 additions and one multiply-add.
+// The tap pattern is the same for a whole warp (one row of one parity of i,
+// one layer at a time), so the selections below do not diverge; the taps
+// are loaded without a branch and layers go in chunks of U as above.
 template <typename T, bool HX, bool HY>
 __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer tr,
                                                      const T* __restrict__ ec,
@@ -219,9 +254,10 @@ __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer 
   if (i < 1 || i > gf.Nx - 2 || j < 1 || j > gf.Ny - 2) return;
   constexpr int NA = HX ? 2 : 1, NB = HY ? 2 : 1;
   int ci[2], cj[2];
-  T ax[2], ay[2];
+  float ax[2], ay[2];
   hpair(HX ? 1 : 0, gf.Nx, gc.Nx, i, ci[0], ax[0], ci[1], ax[1]);
   hpair(HY ? 1 : 0, gf.Ny, gc.Ny, j, cj[0], ay[0], cj[1], ay[1]);
+  const bool two_x = HX && ci[0] != ci[1], two_y = HY && cj[0] != cj[1];
   int64_t hoff[NB][NA];
 #pragma unroll
   for (int b = 0; b < NB; ++b)
@@ -232,14 +268,14 @@ __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer 
   const int kend = gf.Nz - 1;  // free layers 0 .. Nz-2
   constexpr int U = NA * NB >= 4 ? 2 : 4;
   for (int k0 = 0; k0 < kend; k0 += U) {
-    T xv[U], ev[U][2][NB][NA], az[U][2];
+    T xv[U], ev[U][2][NB][NA];
+    bool two_z[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int k = min(k0 + u, kend - 1);
       xv[u] = x[(int64_t)k * gf.PP + own];
       const int ck[2] = {tr.kc0[k], tr.kc1[k]};
-      az[u][0] = (T)tr.kw0[k];
-      az[u][1] = (T)tr.kw1[k];
+      two_z[u] = ck[0] != ck[1];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const T* el = ec + (int64_t)ck[c] * gc.PP;
@@ -251,17 +287,19 @@ __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer 
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      T sv = T(0);
+      T sz[2];
 #pragma unroll
-      for (int c = 0; c < 2; ++c)
+      for (int c = 0; c < 2; ++c) {
+        T sy[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          T row = T(0);
-#pragma unroll
-          for (int a = 0; a < NA; ++a) row += (HX ? ax[a] : T(1)) * ev[u][c][b][a];
-          sv += ((HY ? ay[b] : T(1)) * az[u][c]) * row;
-        }
-      if (k0 + u < kend) x[(int64_t)(k0 + u) * gf.PP + own] = xv[u] + sv;
+        for (int b = 0; b < NB; ++b)
+          sy[b] = (HX && two_x) ? ev[u][c][b][0] + ev[u][c][b][NA - 1] : ev[u][c][b][0];
+        sz[c] = (HY && two_y) ? sy[0] + sy[NB - 1] : sy[0];
+      }
+      const T s = two_z[u] ? sz[0] + sz[1] : sz[0];
+      const int m = (int)two_x + (int)two_y + (int)two_z[u];
+      const T w = m == 0 ? T(1) : (m == 1 ? T(0.5) : (m == 2 ? T(0.25) : T(0.125)));
+      if (k0 + u < kend) x[(int64_t)(k0 + u) * gf.PP + own] = madd(w, s, xv[u]);
     }
   }
 }
@@ -277,7 +315,9 @@ cudaError_t launch_residual(const Grid& g, const T* C, const T* f, const T* x, T
                             double* partials, int cap, int* nblocks, cudaStream_t st) {
   dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
   if (partials && (int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
-  if (partials)
+  if (partials && !x)  // x = 0
+    k_residual<T, 5><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, partials);
+  else if (partials)
     k_residual<T, 0><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, partials);
   else
     k_residual<T, 3><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, r, nullptr, nullptr, nullptr);
@@ -297,7 +337,11 @@ cudaError_t launch_residual_mixed(const Grid& g, const double* C, const double* 
                                   int cap, int* nblocks, cudaStream_t st) {
   dim3 grd((g.H + 31) / 32, (g.Ny + 3) / 4, 2);
   if (partials && (int64_t)grd.x * grd.y * grd.z > cap) return cudaErrorInvalidValue;
-  k_residual<double, 1><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, nullptr, r32, e32, partials); count_launches(1);
+  if (x)
+    k_residual<double, 1><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, nullptr, r32, e32, partials);
+  else
+    k_residual<double, 4><<<grd, dim3(32, 4), 0, st>>>(g, C, f, x, nullptr, r32, e32, partials);
+  count_launches(1);
   if (nblocks) *nblocks = (int)(grd.x * grd.y * grd.z);
   return cudaGetLastError();
 }

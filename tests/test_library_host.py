@@ -192,3 +192,16 @@ def test_batch_rejects_bad_arguments_without_gpu():
     finally:
         m.mcwind_plan_destroy(h)
         m.mcwind_plan_destroy(hc)
+
+
+def test_plan_query_reports_the_check_interval_in_use():
+    """cycles_per_check 0 means the default interval: 6 V-cycles per float64
+    check in mixed precision, 1 in float64; an explicit value is kept."""
+    h3 = [5.0, 6.0, 7.2, 8.64]
+    for prec, given, want in ((m.PREC_MIXED, 0, 6), (m.PREC_F64, 0, 1), (m.PREC_MIXED, 3, 3)):
+        h, _ = m.mcwind_plan_create(16, 12, 4, (1, 1, 1), 30.0, h3,
+                                    m.default_options(precision=prec, cycles_per_check=given))
+        try:
+            assert m.plan_options(h).cycles_per_check == want
+        finally:
+            m.lib().mcwind_plan_destroy(h)
