@@ -54,10 +54,18 @@ FP32_OPS_RECOVER = 1811.0
 FP32_OPS_LOAD_SEPARABLE = 51 * 12.0
 # FP32 pipe: 128 lanes per SM x 152 SMs x 2.07 GHz maximum SM clock
 FP32_PIPE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per unit of a launch, from one ncu capture of the
-# 600x600x15 case, scaled by the units of the full launch: FP32 smoother,
-# bytes per node of the column group.
-TRAFFIC_PER_UNIT = {}
+# Float64 element kernels (element_arith = ARITH_F64, the plain FP64 form):
+# float64 thread instructions per element of the modal stiffness and load
+# vector, counted by ncu on the 600x600x15 case (DADD + DFMA + DMUL).
+FP64_OPS_STIFFNESS = 1213.0
+FP64_OPS_LOAD = 665.0
+# DRAM bytes (read + write) per unit of a launch, from one ncu capture of a
+# smaller case of the same kernel, scaled by the units of the full launch:
+# separable float32 smoother, bytes per free node of the column group
+# (1200x1200x15: 189.8 MB per group launch of 5.39 M nodes).
+TRAFFIC_PER_UNIT = {"smooth_fine": (35.2, "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                          "1200x1200x15 group launch, scaled per group node",
+                                    "separable")}
 
 
 def parse():
@@ -281,7 +289,8 @@ def read_profile(m, plan):
     return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}
 
 
-def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep_rhs=True):
+def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep_rhs=True,
+                element_f64=False, with_recovery=True):
     """Algorithmic units of every kernel class over the timed region.
 
     levels: the plan's level descriptions (Nx, Ny, Nz, hx, hy); solves: the
@@ -371,16 +380,24 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep
         # load vector: u0 pairs in, f out, the column factors once
         U["rhs"] = [["hbm", nsolve * (48 + 24 + 8) * nodes[0] + nsolve * 45 * 8.0 * fcols[0]],
                     ["alu", nsolve * FP32_OPS_LOAD_SEPARABLE * nodes[0]]]
+    elif element_f64:
+        U["rhs"] = [["fp64", nsolve * FP64_OPS_LOAD * n_elem]]
     else:
         U["rhs"] = [["alu", nsolve * FP32_OPS_LOAD * n_elem]]
     if separable:
         # the finest float64 rows expanded from the factors in float pairs: 27
         # coefficients and 1/diag written per node, the column factors read once
         U["assemble"] = [["hbm", nsolve / 2 * (28 * 8.0 * nodes[0] + 36 * 8.0 * nodes[0] / levels[0]["Nz"])]]
+    elif element_f64:
+        U["assemble"] = [["fp64", nsolve / 2 * FP64_OPS_STIFFNESS * n_elem]]
     else:
         U["assemble"] = [["alu", nsolve / 2 * FP32_OPS_STIFFNESS * n_elem]]
-    U["recover"] = [["hbm", nsolve * ((8 + 24 + 24) * nodes[0] + 24.0 * n_elem)],
-                    ["alu", nsolve * FP32_OPS_RECOVER * n_elem]]
+    if separable:
+        # lambda and u0 read, u written (the column form splits in registers)
+        U["recover"] = [["hbm", nsolve * ((8 + 24) * nodes[0] + 24.0 * n_elem)]]
+    else:
+        U["recover"] = [["hbm", nsolve * ((8 + 24 + 24) * nodes[0] + 24.0 * n_elem)],
+                        ["alu", nsolve * FP32_OPS_RECOVER * n_elem]]
     # Galerkin products per assembly: of the column factors (separable: 36 float64
     # values per column read and written per horizontal stage, and the float32
     # tiles), or of the stored rows (28 float64 values per node in and out per
@@ -409,9 +426,13 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep
         setup += sum(28 * 12.0 * nn for nn in nodes)  # float32 copies
     U["setup"] = [["hbm", n_asm * setup]]
     # layout conversions and norms per solve: |f| (8 B per node), lambda out
-    # (8 in, 8 out), lambda in for warm starts; per recovery lambda and u0 split
-    # into float pairs (16 and 48 B per node)
-    U["other"] = [["hbm", nsolve * (8 + 16 + 16 + 64) * nodes[0] - nsolve / 2 * 16 * nodes[0]]]
+    # (8 in, 8 out), lambda in for warm starts (8 in, 8 out); per recovery of
+    # the stored form lambda and u0 split into float pairs (16 and 48 B per node)
+    n_warm = nsolve - (nsolve + 1) // 2
+    other = nsolve * (8 + 16) * nodes[0] + n_warm * 16.0 * nodes[0]
+    if not separable and with_recovery:
+        other += nsolve * 64.0 * nodes[0]
+    U["other"] = [["hbm", other]]
     return {k: v for k, v in U.items() if v}
 
 
@@ -858,7 +879,8 @@ def main():
     if prof_f64:
         nc64 = ((f64_levels[-1]["Nx"] - 2) * (f64_levels[-1]["Ny"] - 2) * (f64_levels[-1]["Nz"] - 1))
         roof_f64 = roofs(prof_f64, class_units(f64_levels, False, False, f64_solves,
-                                               (plan_nu[0], plan_nu[1]), 1, n_elem, nc64))
+                                               (plan_nu[0], plan_nu[1]), 1, n_elem, nc64,
+                                               element_f64=True, with_recovery=False))
     dom = max((k for k in prof_main if prof_main[k][1] > 0), key=lambda k: prof_main[k][0])
     dom_roof = dict(roof_kernels.get(dom, {"bound": None}))
     dom_roof["kernel"] = dom
