@@ -72,14 +72,15 @@ __host__ __device__ inline float float_of_i29(int r) {
 // of df_of.
 __host__ __device__ inline float2 split_bits(double x) {
 #ifdef __CUDA_ARCH__
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
 #else
   unsigned long long u;
   __builtin_memcpy(&u, &x, 8);
-#endif
   const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
+#endif
   const int e = (int)((h32 >> 20) & 0x7FFu);
-  if ((u << 1) == 0ull) {
+  // zero test on the two 32-bit words
+  if (((h32 << 1) | l32) == 0u) {
 #ifdef __CUDA_ARCH__
     return make_float2(__uint_as_float(h32), 0.0f);
 #else
@@ -115,9 +116,10 @@ __host__ __device__ inline float2 split_bits(double x) {
 __device__ __forceinline__ double to_double(dflt a) { return (double)a.hi + (double)a.lo; }
 
 // hi + lo rounded to the nearest double (ties to even), the value to_double
-// gives, formed in integer arithmetic so that it takes no double-pipe
-// instruction.  The pair must be normalized (|lo| <= ulp(hi)/2, as every
-// sum and product below leaves it).  |hi| as a double is its bit pattern
+// gives, formed in integer arithmetic and one float-to-integer conversion
+// (GB300 issues that on the double pipe; there is no double arithmetic).
+// The pair must be normalized (|lo| <= ulp(hi)/2, as every sum and product
+// below leaves it).  |hi| as a double is its bit pattern
 // with the exponent rebased and the 23 fraction bits moved up by 29; lo is
 // then a whole number k of units of the double's last place in hi's binade
 // (|k| <= 2^28), added to the magnitude's bit pattern.  That addition never
@@ -176,12 +178,12 @@ __host__ __device__ inline double pair_to_double(float2 v) { return pair_to_doub
 // infinities and NaN take the conversion.
 __host__ __device__ inline float float_of_bits(double x) {
 #ifdef __CUDA_ARCH__
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
 #else
   unsigned long long u;
   __builtin_memcpy(&u, &x, 8);
-#endif
   const unsigned h32 = (unsigned)(u >> 32), l32 = (unsigned)u;
+#endif
   const unsigned sign = h32 & 0x80000000u;
   const int e = (int)((h32 >> 20) & 0x7FFu);
   unsigned fb;

@@ -57,24 +57,23 @@ __device__ __forceinline__ void pmac2(float& sh, float& sl, float2 a, float2 b) 
 // coordinate magnitude involved (the generator's rounding of z_s + zeta is
 // far below it).  Standard layout.  One thread per node above the ground
 // layer (blockIdx.z = k - 1); equal X and Y are recognised by their bits,
-// and "small" is decided on the exponents: |d| < 2^-33 max (one float64
-// subtraction per node besides the two of the z test, which matters at the
-// float64 issue rate).
-__device__ __forceinline__ long long mag_bits(double v) {
-  return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL;
-}
+// and "small" is decided on the exponents, |d| < 2^-33 max, in 32-bit
+// integer arithmetic on the high words (on GB300 the double pipe, which
+// also issues some 64-bit integer instructions, runs at 1/64 of the float
+// rate): two float64 subtractions per node for the z test.
+__device__ __forceinline__ unsigned mag_hi(double v) { return (unsigned)__double2hiint(v) & 0x7FFFFFFFu; }
 
 __global__ void k_shift_check(int Nx, int Ny, int Nz, const double* __restrict__ X,
                               const double* __restrict__ Y, const double* __restrict__ Z,
                               int* flag) {
   __shared__ double zeta;
-  __shared__ long long mlay;
+  __shared__ unsigned mlay;
   const int k = (int)blockIdx.z + 1;
   const int64_t lay = (int64_t)Nx * Ny;
   if (threadIdx.x == 0) {
     const double zr = Z[k * lay], zb = Z[0];
     zeta = zr - zb;
-    mlay = max(mag_bits(zr), mag_bits(zb));
+    mlay = max(mag_hi(zr), mag_hi(zb));
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,12 +82,14 @@ __global__ void k_shift_check(int Nx, int Ny, int Nz, const double* __restrict__
   const int64_t c = (int64_t)j * Nx + i;
   const double x0 = X[c], y0 = Y[c], z0 = Z[c];
   const double xk = X[k * lay + c], yk = Y[k * lay + c], zk = Z[k * lay + c];
-  const long long m = max(max(mag_bits(x0), mag_bits(y0)), max(max(mag_bits(z0), mag_bits(zk)), mlay));
-  const int lim = (int)(m >> 52) - 34;  // biased exponent bound of a small difference
-  auto small = [lim](double d) { return (int)(mag_bits(d) >> 52) <= lim; };
+  const unsigned m = max(max(mag_hi(x0), mag_hi(y0)), max(max(mag_hi(z0), mag_hi(zk)), mlay));
+  const int lim = (int)(m >> 20) - 34;  // biased exponent bound of a small difference
+  auto small = [lim](double d) { return (int)(mag_hi(d) >> 20) <= lim; };
   bool ok = small((zk - z0) - zeta);
-  if (__double_as_longlong(xk) != __double_as_longlong(x0)) ok = ok && small(xk - x0);
-  if (__double_as_longlong(yk) != __double_as_longlong(y0)) ok = ok && small(yk - y0);
+  if (__double2hiint(xk) != __double2hiint(x0) || __double2loint(xk) != __double2loint(x0))
+    ok = ok && small(xk - x0);
+  if (__double2hiint(yk) != __double2hiint(y0) || __double2loint(yk) != __double2loint(y0))
+    ok = ok && small(yk - y0);
   if (!ok) atomicOr(flag, kShiftFlag);
 }
 
@@ -457,8 +458,11 @@ __global__ void __launch_bounds__(128) k_sep_expand(Grid g, const double* __rest
     for (int s2 = 0; s2 < 9; ++s2) {
 #pragma unroll
       for (int dk = 0; dk < 3; ++dk) {
-        float sh = 0.0f, sl = 0.0f;
-        pmac2(sh, sl, P[s2], v[dk]);
+        // the first product seeds the sum: its rounding error is the low part
+        float sh = P[s2].x * v[dk].x;
+        float sl = fmaf(P[s2].x, v[dk].x, -sh);
+        sl = fmaf(P[s2].x, v[dk].y, sl);
+        sl = fmaf(P[s2].y, v[dk].x, sl);
         pmac2(sh, sl, R[s2], v[3 + dk]);
         if (dk == 0) pmac2(sh, sl, S[s2], v[6]);
         if (dk == 2) pmac2(sh, sl, S[s2], v[7]);
@@ -623,6 +627,9 @@ __global__ void __launch_bounds__(32 * (kGsR + 1)) k_gs_sep_staged(
   float Pb = 0.0f, Sb = 0.0f, Rb = 0.0f, Pc = 0.0f, Sc = 0.0f, Rc = 0.0f;
   float yT0 = 0.0f;  // T-sum of the ground layer (its only row with B != 0)
   float xb = 0.0f;
+  // unrolled by the period of the behind / current / ahead window, so the
+  // window moves by renaming registers
+#pragma unroll 3
   for (int t = 0; t <= nlay; ++t) {
     float Pt = 0.0f, St = 0.0f, Rt = 0.0f, xt = 0.0f;
     if (t < nlay) {
