@@ -96,7 +96,8 @@ __global__ void k_shift_check(int Nx, int Ny, int Nz, const double* __restrict__
 // Horizontal factors of the cells of one parity class (cell (ci, cj) with
 // ci & 1 = cls & 1, cj & 1 = cls >> 1), added into the float64 planes of
 // their 4 corner columns: cells of one class share no corner, and the four
-// classes run in order, so every sum is formed in one fixed order.  2 x 2
+// classes run in order, so every sum is formed in one fixed order (the adds
+// are L2 reductions, one per address and launch: the same sums, bitwise).  2 x 2
 // Gauss points in (xi1, xi2), in arithmetic R (float64 or float pairs).
 // Corner p = a + 2b is node (ci + a, cj + b) of the ground layer (standard
 // layout).  P and R are symmetric, so only their upper triangles are formed.
@@ -170,10 +171,12 @@ __global__ void __launch_bounds__(128) k_hfactor_cells(Grid g, int cls, const do
       const int s2 = ((q & 1) - (p & 1) + 1) + 3 * ((q >> 1) - (p >> 1) + 1);
       const int lo = p < q ? p : q, hi = p < q ? q : p;
       const int t = lo * 4 - lo * (lo - 1) / 2 + (hi - lo);  // tri(lo, hi)
-      H[(0 * 9 + s2) * g.PP + col] += A::to_double(P[t]);
-      H[(1 * 9 + s2) * g.PP + col] -= A::to_double(Q[p][q]);
-      H[(2 * 9 + s2) * g.PP + col] -= A::to_double(Q[q][p]);
-      H[(3 * 9 + s2) * g.PP + col] += A::to_double(Rr[t]);
+      // one add per address and launch (cells of a class share no column),
+      // issued as reductions in L2 so the cell does not wait for the reads
+      atomicAdd(&H[(0 * 9 + s2) * g.PP + col], A::to_double(P[t]));
+      atomicAdd(&H[(1 * 9 + s2) * g.PP + col], -A::to_double(Q[p][q]));
+      atomicAdd(&H[(2 * 9 + s2) * g.PP + col], -A::to_double(Q[q][p]));
+      atomicAdd(&H[(3 * 9 + s2) * g.PP + col], A::to_double(Rr[t]));
     }
   }
 }
@@ -777,6 +780,8 @@ __global__ void __launch_bounds__(32 * (kGsR + 1)) k_residual_sep_staged(
   float T0 = 0.0f;
   int Kcur = 0;
   float accLo = 0.0f, accHi = 0.0f;
+  // unrolled by the window's period (the unfused form keeps its registers)
+#pragma unroll (FUSE ? 3 : 1)
   for (int t = 0; t <= nlay; ++t) {
     float Pt = 0.0f, St = 0.0f, Rt = 0.0f;
     if (t < nlay) {

@@ -242,8 +242,9 @@ __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
 // n = 1..8 taps share the weight 2^-m (m = directions with two taps) and
 // x + 2^-m (sum of the taps) costs n - 1 additions and one multiply-add.
 // The tap pattern is the same for a whole warp (one row of one parity of i,
-// one layer at a time), so neither the selections nor the loads of second
-// taps diverge; layers go in chunks of U as above.
+// one layer at a time), so the selections below do not diverge; every tap
+// is loaded without a branch (a missing second tap repeats the first, an L1
+// hit) and layers go in chunks of U as above.
 template <typename T, bool HX, bool HY>
 __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer tr,
                                                      const T* __restrict__ ec,
@@ -282,11 +283,7 @@ __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer 
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-          for (int a = 0; a < NA; ++a) {
-            // a second tap only where that direction has two (warp-uniform)
-            const bool need = (c == 0 || two_z[u]) && (b == 0 || two_y) && (a == 0 || two_x);
-            ev[u][c][b][a] = need ? el[hoff[b][a]] : T(0);
-          }
+          for (int a = 0; a < NA; ++a) ev[u][c][b][a] = el[hoff[b][a]];
       }
     }
 #pragma unroll
