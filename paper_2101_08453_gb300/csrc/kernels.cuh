@@ -118,7 +118,8 @@ cudaError_t launch_rap_stage(int dim, const Grid& gin, const Grid& gout, const T
 cudaError_t launch_coarse_index(const Grid& g, int* cfree, cudaStream_t st);
 cudaError_t launch_dense_gather(const Grid& g, const double* C, const int* cfree, int n,
                                 double* A, cudaStream_t st);
-// Gauss-Jordan inversion, n steps ping-ponging between A and B; result in *result
+// Gauss-Jordan inversion in place in A (blocks of 16 pivots, B holds the
+// step's panels: 256 + 32 n doubles); *result = A
 cudaError_t launch_dense_invert(double* A, double* B, int n, double** result, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dense_solve(const double* Ainv, int n, const int* cfree, const T* f, T* x,
