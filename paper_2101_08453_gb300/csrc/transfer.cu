@@ -1,5 +1,6 @@
 // Residual, restriction and prolongation (Sec. 3, Eq. 7), and the float64
 // refinement kernels of the mixed-precision solve.
+#include <climits>
 #include "kernels.cuh"
 
 namespace mcw {
@@ -156,16 +157,16 @@ __device__ __forceinline__ double madd(double a, double b, double c) { return fm
 // the float64 transfers).  Every tap is loaded without a branch (a tap
 // outside the stencil reads a valid neighbour), and layers go in chunks of
 // U, so a thread has all loads of U nodes in flight.
-template <typename T, bool HX, bool HY>
+template <typename T, bool HX, bool HY, typename Ix>
 __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
                                                   const T* __restrict__ r, T* __restrict__ fc) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int I = 2 * h + (int)blockIdx.z;
   if (I >= gc.Nx || J >= gc.Ny) return;
-  const int64_t own = (int64_t)J * gc.RP + (int64_t)(I & 1) * gc.H + (I >> 1);
+  const Ix own = (Ix)J * (Ix)gc.RP + (Ix)(I & 1) * (Ix)gc.H + (Ix)(I >> 1);
   if (I < 1 || I > gc.Nx - 2 || J < 1 || J > gc.Ny - 2) {
-    for (int K = 0; K < gc.Nz; ++K) fc[(int64_t)K * gc.PP + own] = T(0);
+    for (int K = 0; K < gc.Nz; ++K) fc[(Ix)K * (Ix)gc.PP + own] = T(0);
     return;
   }
   constexpr int NA = HX ? 3 : 1, NB = HY ? 3 : 1;
@@ -175,13 +176,13 @@ __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
   hcoarse(HY ? 1 : 0, gf.Ny, gc.Ny, J, fj, wym, wyp);
   const bool mx = wxm != 0.0f, px = wxp != 0.0f, my = wym != 0.0f, py = wyp != 0.0f;
   // in-layer offsets of the taps (fine columns fi-1..fi+1 are valid: I is interior)
-  int64_t hoff[NB][NA];
+  Ix hoff[NB][NA];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
       const int ii = HX ? fi + a - 1 : fi, jj = HY ? fj + b - 1 : fj;
-      hoff[b][a] = (int64_t)jj * gf.RP + (int64_t)(ii & 1) * gf.H + (ii >> 1);
+      hoff[b][a] = (Ix)jj * (Ix)gf.RP + (Ix)(ii & 1) * (Ix)gf.H + (Ix)(ii >> 1);
     }
   }
   const int Kend = gc.Nz - 1;  // the top layer is Dirichlet
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
       const int kl[3] = {mz[u] ? fk - 1 : fk, fk, pz[u] ? fk + 1 : fk};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const T* rl = r + (int64_t)kl[c] * gf.PP;
+        const T* rl = r + (Ix)kl[c] * (Ix)gf.PP;
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -231,10 +232,10 @@ __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
       }
       const T m = mz[u] ? col[0] : T(0), pl = pz[u] ? col[2] : T(0);
       const T out = madd(T(0.5), m + pl, col[1]);
-      if (K0 + u < Kend) fc[(int64_t)(K0 + u) * gc.PP + own] = out;
+      if (K0 + u < Kend) fc[(Ix)(K0 + u) * (Ix)gc.PP + own] = out;
     }
   }
-  fc[(int64_t)Kend * gc.PP + own] = T(0);
+  fc[(Ix)Kend * (Ix)gc.PP + own] = T(0);
 }
 
 // x += P e_c (Eq. 7) over one fine column (i, j), all free k.  Per direction
@@ -245,7 +246,9 @@ __global__ void __launch_bounds__(128) k_restrict(Grid gf, Grid gc, Transfer tr,
 // one layer at a time), so the selections below do not diverge; every tap
 // is loaded without a branch (a missing second tap repeats the first, an L1
 // hit) and layers go in chunks of U as above.
-template <typename T, bool HX, bool HY>
+// I: the index type of offsets within a level (int when both levels have
+// fewer than 2^31 entries: 32-bit address arithmetic)
+template <typename T, bool HX, bool HY, typename I>
 __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer tr,
                                                      const T* __restrict__ ec,
                                                      T* __restrict__ x) {
@@ -259,13 +262,13 @@ __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer 
   hpair(HX ? 1 : 0, gf.Nx, gc.Nx, i, ci[0], ax[0], ci[1], ax[1]);
   hpair(HY ? 1 : 0, gf.Ny, gc.Ny, j, cj[0], ay[0], cj[1], ay[1]);
   const bool two_x = HX && ci[0] != ci[1], two_y = HY && cj[0] != cj[1];
-  int64_t hoff[NB][NA];
+  I hoff[NB][NA];
 #pragma unroll
   for (int b = 0; b < NB; ++b)
 #pragma unroll
     for (int a = 0; a < NA; ++a)
-      hoff[b][a] = (int64_t)cj[b] * gc.RP + (int64_t)(ci[a] & 1) * gc.H + (ci[a] >> 1);
-  const int64_t own = (int64_t)j * gf.RP + (int64_t)(i & 1) * gf.H + (i >> 1);
+      hoff[b][a] = (I)cj[b] * (I)gc.RP + (I)(ci[a] & 1) * (I)gc.H + (I)(ci[a] >> 1);
+  const I own = (I)j * (I)gf.RP + (I)(i & 1) * (I)gf.H + (I)(i >> 1);
   const int kend = gf.Nz - 1;  // free layers 0 .. Nz-2
   constexpr int U = NA * NB >= 4 ? 2 : 4;
   for (int k0 = 0; k0 < kend; k0 += U) {
@@ -274,12 +277,12 @@ __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int k = min(k0 + u, kend - 1);
-      xv[u] = x[(int64_t)k * gf.PP + own];
+      xv[u] = x[(I)k * (I)gf.PP + own];
       const int ck[2] = {tr.kc0[k], tr.kc1[k]};
       two_z[u] = ck[0] != ck[1];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const T* el = ec + (int64_t)ck[c] * gc.PP;
+        const T* el = ec + (I)ck[c] * (I)gc.PP;
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(128) k_prolong_add(Grid gf, Grid gc, Transfer 
       const T s = two_z[u] ? sz[0] + sz[1] : sz[0];
       const int m = (int)two_x + (int)two_y + (int)two_z[u];
       const T w = m == 0 ? T(1) : (m == 1 ? T(0.5) : (m == 2 ? T(0.25) : T(0.125)));
-      if (k0 + u < kend) x[(int64_t)(k0 + u) * gf.PP + own] = madd(w, s, xv[u]);
+      if (k0 + u < kend) x[(I)(k0 + u) * (I)gf.PP + own] = madd(w, s, xv[u]);
     }
   }
 }
@@ -365,10 +368,19 @@ template <typename T>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, const Transfer& tr, const T* r,
                             T* fc, cudaStream_t st) {
   const dim3 grd = column_grid(gc), blk(32, 4);
-  if (tr.hx && tr.hy) k_restrict<T, true, true><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
-  else if (tr.hx) k_restrict<T, true, false><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
-  else if (tr.hy) k_restrict<T, false, true><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
-  else k_restrict<T, false, false><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+  // 32-bit offsets within a level when both levels have fewer than 2^31 entries
+  const bool small = gf.total < (int64_t)INT_MAX && gc.total < (int64_t)INT_MAX;
+  if (small) {
+    if (tr.hx && tr.hy) k_restrict<T, true, true, int><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+    else if (tr.hx) k_restrict<T, true, false, int><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+    else if (tr.hy) k_restrict<T, false, true, int><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+    else k_restrict<T, false, false, int><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+  } else {
+    if (tr.hx && tr.hy) k_restrict<T, true, true, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+    else if (tr.hx) k_restrict<T, true, false, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+    else if (tr.hy) k_restrict<T, false, true, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+    else k_restrict<T, false, false, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, r, fc);
+  }
   count_launches(1);
   return cudaGetLastError();
 }
@@ -376,10 +388,18 @@ template <typename T>
 cudaError_t launch_prolong_add(const Grid& gf, const Grid& gc, const Transfer& tr, const T* ec,
                                T* x, cudaStream_t st) {
   const dim3 grd = column_grid(gf), blk(32, 4);
-  if (tr.hx && tr.hy) k_prolong_add<T, true, true><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
-  else if (tr.hx) k_prolong_add<T, true, false><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
-  else if (tr.hy) k_prolong_add<T, false, true><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
-  else k_prolong_add<T, false, false><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+  const bool small = gf.total < (int64_t)INT_MAX && gc.total < (int64_t)INT_MAX;
+  if (small) {
+    if (tr.hx && tr.hy) k_prolong_add<T, true, true, int><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+    else if (tr.hx) k_prolong_add<T, true, false, int><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+    else if (tr.hy) k_prolong_add<T, false, true, int><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+    else k_prolong_add<T, false, false, int><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+  } else {
+    if (tr.hx && tr.hy) k_prolong_add<T, true, true, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+    else if (tr.hx) k_prolong_add<T, true, false, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+    else if (tr.hy) k_prolong_add<T, false, true, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+    else k_prolong_add<T, false, false, int64_t><<<grd, blk, 0, st>>>(gf, gc, tr, ec, x);
+  }
   count_launches(1);
   return cudaGetLastError();
 }
