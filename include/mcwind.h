@@ -207,8 +207,13 @@ int mcwind_plan_level(mcwind_plan plan, int level, int dims[3], int* hx, int* hy
  * workspace: device, >= workspace_bytes, 256-byte aligned.  X, Y, Z: device
  * node coordinates [nz+1][ny+1][nx+1].  Builds the 27-point stiffness
  * stencil by 2x2x2 Gauss quadrature, the Galerkin operators of all coarser
- * levels and the coarsest direct solver.  Synchronizes the stream once at the
- * end to report EGEOM when an element is inverted or degenerate. */
+ * levels and the coarsest direct solver (MCWIND_OP_SEPARABLE: the column and
+ * layer factors of every level, the finest and coarsest float64 rows).  The
+ * plan keeps the X, Y, Z pointers: they must stay valid and unchanged until
+ * the plan is assembled again or destroyed (the load vector, the recovery,
+ * the weak divergence and the gradient calls read them).  Synchronizes the
+ * stream once at the end to report EGEOM when an element is inverted or
+ * degenerate and ESHIFT when a separable plan's grid is not in shift form. */
 int mcwind_assemble(mcwind_plan plan, void* workspace, const double* X, const double* Y,
                     const double* Z, void* stream);
 
