@@ -391,7 +391,10 @@ def class_units(levels, mixed, separable, solves, nu, cpc, n_elem, n_coarse, sep
     elif element_f64:
         U["assemble"] = [["fp64", nsolve / 2 * FP64_OPS_STIFFNESS * n_elem]]
     else:
-        U["assemble"] = [["alu", nsolve / 2 * FP32_OPS_STIFFNESS * n_elem]]
+        # float pairs: their own FP32-pipe count, and the float64 form's work
+        # (1213 FP64 instructions per element) against the FP64 rate
+        U["assemble"] = [["alu", nsolve / 2 * FP32_OPS_STIFFNESS * n_elem],
+                         ["fp64_equiv", nsolve / 2 * FP64_OPS_STIFFNESS * n_elem]]
     if separable:
         # lambda and u0 read, u written (the column form splits in registers)
         U["recover"] = [["hbm", nsolve * ((8 + 24) * nodes[0] + 24.0 * n_elem)]]
@@ -850,14 +853,20 @@ def main():
             ms, n = profile.get(k, (0.0, 0))
             if n == 0 or ms <= 0.0:
                 continue
-            cand = []
+            cand, info = [], {}
             for bound, total in bounds:
-                unit, scale, peak = UNITS[bound]
+                # "fp64_equiv": the float64 form's work of a float-pair kernel,
+                # against the FP64 rate; reported beside the bound, never as it
+                unit, scale, peak = UNITS["fp64" if bound == "fp64_equiv" else bound]
                 ach = total / (ms / 1e3) / scale
+                if bound == "fp64_equiv":
+                    info[bound] = ach / peak
+                    continue
                 cand.append({"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                              "frac": ach / peak})
             best = dict(max(cand, key=lambda c: c["frac"]))
             best["other_bounds"] = {c["bound"]: c["frac"] for c in cand if c["bound"] != best["bound"]}
+            best["other_bounds"].update(info)
             best["ms"] = ms
             best["launches"] = n
             best["ms_per_launch"] = ms / n
