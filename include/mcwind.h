@@ -80,8 +80,8 @@ enum { MCWIND_OP_STORED = 0, MCWIND_OP_SEPARABLE = 1 };
 #define MCWIND_HIST 256
 
 typedef struct {
-  /* Gauss-Seidel sweeps before and after the coarse correction (Sec. 3,
-     "four smoothing steps per cycle": default 2 and 2). */
+  /* Gauss-Seidel sweeps before and after the coarse correction (Sec. 3
+     uses four smoothing steps in a cycle: default 2 and 2). */
   int nu_pre, nu_post;
   /* Semicoarsening ratio (Sec. 3): MCWIND_RULE_PAPER uses h3/(h1 a3) as
      printed; MCWIND_RULE_OPERATOR (default) uses a3 h3/(a1 h1), the ratio

@@ -1,4 +1,4 @@
-// Direct solve on the coarsest grid (Sec. 3: "solved by a direct method").
+// Direct solve on the coarsest grid (Sec. 3: the coarsest problem is solved directly).
 // The free block of the coarsest operator (n <= 4096 unknowns, numbered
 // k-major over the free nodes) is gathered into a dense matrix and inverted
 // once, at assembly, by Gauss-Jordan elimination without pivoting (the
