@@ -205,3 +205,35 @@ def test_plan_query_reports_the_check_interval_in_use():
             assert m.plan_options(h).cycles_per_check == want
         finally:
             m.lib().mcwind_plan_destroy(h)
+
+
+def test_plan_bound_wrappers_refuse_short_buffers():
+    """Every plan-bound wrapper checks each tensor's element count against
+    the plan before any pointer reaches the library (no device needed)."""
+    torch = pytest.importorskip("torch")
+    h3 = [5.0, 6.0, 7.2, 8.64]
+    h, _ = m.mcwind_plan_create(16, 12, 4, (1, 1, 1), 30.0, h3,
+                                m.default_options(precision=m.PREC_MIXED, coarsest_max=64))
+    try:
+        assert m.mcwind_plan_num_levels(h) >= 2
+        nodes = 17 * 13 * 5
+        cells = 16 * 12 * 4
+        ok = torch.zeros(nodes, dtype=torch.float64)
+        short = torch.zeros(nodes - 1, dtype=torch.float64)
+        u0 = torch.zeros(3 * nodes, dtype=torch.float64)
+        calls = [
+            ("lam", lambda: m.mcwind_solve(h, u0, short)),
+            ("u0", lambda: m.mcwind_solve(h, u0[:-1], ok)),
+            ("u", lambda: m.mcwind_recover(h, u0, ok, torch.zeros(3 * cells - 1, dtype=torch.float64))),
+            ("f", lambda: m.mcwind_rhs(h, u0, short)),
+            ("x", lambda: m.mcwind_level_residual(h, 0, m.PREC_MIXED, short, ok, ok)),
+            ("r", lambda: m.mcwind_level_residual(h, 0, m.PREC_MIXED, ok, ok, short)),
+            ("x", lambda: m.mcwind_level_smooth(h, 0, m.PREC_MIXED, short, ok, 1, m.FORWARD)),
+            ("fc", lambda: m.mcwind_level_residual_restrict(h, 0, m.PREC_MIXED, ok, ok, short)),
+            ("norms", lambda: m.mcwind_residual_norm_noalloc(h, ok, ok, torch.zeros(1, dtype=torch.float64))),
+        ]
+        for name, call in calls:
+            with pytest.raises(ValueError, match=name):
+                call()
+    finally:
+        m.lib().mcwind_plan_destroy(h)
