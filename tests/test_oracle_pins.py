@@ -440,3 +440,119 @@ def test_center_wind_load_vector():
     a = oracle.assemble_f_centers(c, mean, 1)
     b = oracle.assemble_f(c, u0=u0, quad=1)
     assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+def _column_factors(c):
+    """Horizontal factors of a shift-form grid, assembled over the node
+    columns from the ground layer by 2 x 2 Gauss points per cell (weight 1):
+    P_ab = sum grad phi_a . W grad phi_b, Q_ab = sum grad phi_a . W z' phi_b,
+    R_ab = sum (z' . W z' + j2 / a3^2) phi_a phi_b, with J2 the horizontal
+    Jacobian, j2 = det J2, W = adj(J2) diag(a1^-2, a2^-2) adj(J2)^T / j2 and
+    z' the terrain slope, all in the reference coordinates (Sec. 2)."""
+    nx, ny = c.nx, c.ny
+    c1, c2, c3 = (np.asarray(c.a, dtype=float) ** -2)
+    ncol = (nx + 1) * (ny + 1)
+    P, Q, R = (np.zeros((ncol, ncol)) for _ in range(3))
+    sx = np.array([-1.0, 1.0, -1.0, 1.0])
+    sy = np.array([-1.0, -1.0, 1.0, 1.0])
+    gp = 1.0 / np.sqrt(3.0)
+    for cj in range(ny):
+        for ci in range(nx):
+            idx = [(cj + (p >> 1)) * (nx + 1) + ci + (p & 1) for p in range(4)]
+            xs, ys, zs = (np.array([A[0].flat[n] for n in idx]) for A in (c.X, c.Y, c.Z))
+            for e1 in (-gp, gp):
+                for e2 in (-gp, gp):
+                    phi = 0.25 * (1 + sx * e1) * (1 + sy * e2)
+                    grads = np.stack([0.25 * sx * (1 + sy * e2), 0.25 * sy * (1 + sx * e1)], axis=1)
+                    J = np.array([[xs @ grads[:, 0], xs @ grads[:, 1]],
+                                  [ys @ grads[:, 0], ys @ grads[:, 1]]])
+                    zp = zs @ grads
+                    j2 = np.linalg.det(J)
+                    adj = np.array([[J[1, 1], -J[0, 1]], [-J[1, 0], J[0, 0]]])
+                    W = adj @ np.diag([c1, c2]) @ adj.T / j2
+                    blk = np.ix_(idx, idx)
+                    P[blk] += grads @ W @ grads.T
+                    Q[blk] += np.outer(grads @ W @ zp, phi)
+                    R[blk] += (zp @ W @ zp + c3 * j2) * np.outer(phi, phi)
+    return P, Q, R
+
+
+def _layer_factors(h):
+    """Vertical factors: exact 1-D integrals of linear elements of thickness
+    h_l, sum (h/2) m, sum g and sum (2/h) kappa over the layers."""
+    nz = len(h)
+    M, G, Kv = (np.zeros((nz + 1, nz + 1)) for _ in range(3))
+    m = np.array([[2.0, 1.0], [1.0, 2.0]]) / 3.0
+    g = np.array([[-1.0, 1.0], [-1.0, 1.0]]) / 2.0
+    kap = np.array([[1.0, -1.0], [-1.0, 1.0]]) / 2.0
+    for l, hl in enumerate(h):
+        s = slice(l, l + 2)
+        M[s, s] += hl / 2.0 * m
+        G[s, s] += g
+        Kv[s, s] += 2.0 / hl * kap
+    return M, G, Kv
+
+
+@pytest.mark.parametrize("a", [(1.0, 1.0, 1.0), (2.0, 1.0, 0.5)])
+def test_shift_form_stiffness_is_a_sum_of_column_layer_products(a):
+    """On a terrain-following grid in shift form (z = z_s(x, y) + zeta_k) the
+    2x2x2-Gauss stiffness of Eq. 5 equals
+      M (x) P - G (x) Q - G^T (x) Q^T + K_v (x) R
+    exactly (up to rounding): det J = (h/2) j2 and the vertical parts are
+    polynomials the 2-point rule integrates exactly.  The oracle's element
+    loop on a curved grid against the factors formed here."""
+    c = synth.single_hill(6, 5, 3, sigma=60.0, height=30.0, a=a)
+    h = np.diff(c.Z[:, 0, 0])
+    assert np.allclose(c.Z - c.Z[:1], (c.Z[:, 0, 0] - c.Z[0, 0, 0])[:, None, None], atol=1e-9)
+    P, Q, R = _column_factors(c)
+    M, G, Kv = _layer_factors(h)
+    Kref = np.kron(M, P) - np.kron(G, Q) - np.kron(G.T, Q.T) + np.kron(Kv, R)
+    K = oracle.assemble_K(c).toarray()
+    assert np.abs(K - Kref).max() <= 1e-12 * np.abs(K).max()
+    # the terrain matters: the Q terms are not zero on this grid
+    assert np.abs(Q).max() > 1e-3 * np.abs(P).max()
+
+
+def test_shift_form_load_vector_is_a_sum_of_column_layer_products():
+    """The load vector of Eq. 5 (2x2x2 Gauss, u0 trilinear from the nodes) on
+    a shift-form grid: with det J grad N = ((h/2) adj^T grad phi psi -
+    adj^T z' phi psi', j2 phi psi') and u0 interpolated,
+      f = -[(V_M (x) E_x) u_x + (V_M (x) E_y) u_y - (V_G^T (x) F_x) u_x
+            - (V_G^T (x) F_y) u_y + (V_G^T (x) M_z) u_z],
+    E_d = sum (adj^T grad phi_a)_d phi_b, F_d = sum (adj^T z')_d phi_a phi_b,
+    M_z = sum j2 phi_a phi_b over the 2 x 2 points, V_M = sum (h/2) m,
+    V_G = sum g.  Against the oracle's element loop."""
+    c = synth.single_hill(6, 5, 3, sigma=60.0, height=30.0, a=(1.0, 2.0, 0.5))
+    nx, ny = c.nx, c.ny
+    ncol = (nx + 1) * (ny + 1)
+    Ex, Ey, Fx, Fy, Mz = (np.zeros((ncol, ncol)) for _ in range(5))
+    sx = np.array([-1.0, 1.0, -1.0, 1.0])
+    sy = np.array([-1.0, -1.0, 1.0, 1.0])
+    gp = 1.0 / np.sqrt(3.0)
+    for cj in range(ny):
+        for ci in range(nx):
+            idx = [(cj + (p >> 1)) * (nx + 1) + ci + (p & 1) for p in range(4)]
+            xs, ys, zs = (np.array([A[0].flat[n] for n in idx]) for A in (c.X, c.Y, c.Z))
+            for e1 in (-gp, gp):
+                for e2 in (-gp, gp):
+                    phi = 0.25 * (1 + sx * e1) * (1 + sy * e2)
+                    grads = np.stack([0.25 * sx * (1 + sy * e2), 0.25 * sy * (1 + sx * e1)], axis=1)
+                    J = np.array([[xs @ grads[:, 0], xs @ grads[:, 1]],
+                                  [ys @ grads[:, 0], ys @ grads[:, 1]]])
+                    zp = zs @ grads
+                    adjT = np.array([[J[1, 1], -J[1, 0]], [-J[0, 1], J[0, 0]]])  # adj(J2)^T
+                    ag = grads @ adjT.T          # rows: (adj^T grad phi_a)
+                    az = adjT @ zp               # adj^T z'
+                    blk = np.ix_(idx, idx)
+                    Ex[blk] += np.outer(ag[:, 0], phi)
+                    Ey[blk] += np.outer(ag[:, 1], phi)
+                    pp = np.outer(phi, phi)
+                    Fx[blk] += az[0] * pp
+                    Fy[blk] += az[1] * pp
+                    Mz[blk] += np.linalg.det(J) * pp
+    M, G, _ = _layer_factors(np.diff(c.Z[:, 0, 0]))
+    ux, uy, uz = (c.u0[d].ravel() for d in range(3))
+    f_ref = -(np.kron(M, Ex) @ ux + np.kron(M, Ey) @ uy - np.kron(G.T, Fx) @ ux
+              - np.kron(G.T, Fy) @ uy + np.kron(G.T, Mz) @ uz)
+    f = oracle.assemble_f(c)
+    assert np.abs(f - f_ref).max() <= 1e-12 * np.abs(f).max()
