@@ -556,3 +556,39 @@ def test_shift_form_load_vector_is_a_sum_of_column_layer_products():
               - np.kron(G.T, Fy) @ uy + np.kron(G.T, Mz) @ uz)
     f = oracle.assemble_f(c)
     assert np.abs(f - f_ref).max() <= 1e-12 * np.abs(f).max()
+
+
+def test_galerkin_hierarchy_keeps_the_column_layer_form():
+    """Eq. 7 on a shift-form grid: with P = P_z (x) P_y (x) P_x and the free
+    set a product of free layers and free columns, every level's operator is
+    sum_t V_t^l (x) H_t^l with V^{l+1} = P_z^T V^l P_z and H^{l+1} =
+    P_h^T H^l P_h (each masked to its free set).  Against the oracle's
+    Galerkin hierarchy, level by level; and V_G + V_G^T = -e0 e0^T on every
+    level, which leaves three terms above the ground layer."""
+    c = synth.single_hill(8, 8, 4, sigma=60.0, height=30.0)
+    Hy = oracle.Hierarchy(c, coarsest_max=16)
+    assert len(Hy.levels) >= 3
+    P, Q, R = _column_factors(c)
+    M, G, Kv = _layer_factors(np.diff(c.Z[:, 0, 0]))
+    terms = [(M, P), (-G, Q), (-G.T, Q.T), (Kv, R)]
+    for l, lev in enumerate(Hy.levels):
+        Nx, Ny, Nz = lev["Nx"], lev["Ny"], lev["Nz"]
+        ii, jj = np.meshgrid(np.arange(Nx), np.arange(Ny))
+        dh = ((ii >= 1) & (ii <= Nx - 2) & (jj >= 1) & (jj <= Ny - 2)).ravel().astype(float)
+        dv = (np.arange(Nz) <= Nz - 2).astype(float)
+        terms = [(dv[:, None] * V * dv[None, :], dh[:, None] * Hh * dh[None, :]) for V, Hh in terms]
+        Kref = sum(np.kron(V, Hh) for V, Hh in terms)
+        K = Hy.K[l].toarray()
+        assert np.abs(K - Kref).max() <= 1e-12 * np.abs(K).max(), l
+        # the three-term form: V_G + V_G^T = -e0 e0^T on the free layers of
+        # every level (the ground layer is a node layer of every level)
+        B2 = -(terms[1][0] + terms[2][0])
+        E = np.zeros_like(B2)
+        E[0, 0] = -1.0
+        assert np.abs(B2 - E).max() <= 1e-14, l
+        if l + 1 < len(Hy.levels):
+            Px = oracle._p1d_horizontal(Nx, lev["hx"]).toarray()
+            Py = oracle._p1d_horizontal(Ny, lev["hy"]).toarray()
+            Pz = oracle._p1d_from_map(Nz, lev["kmap"]).toarray()
+            Ph = np.kron(Py, Px)
+            terms = [(Pz.T @ V @ Pz, Ph.T @ Hh @ Ph) for V, Hh in terms]
