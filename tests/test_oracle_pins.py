@@ -592,3 +592,34 @@ def test_galerkin_hierarchy_keeps_the_column_layer_form():
             Pz = oracle._p1d_from_map(Nz, lev["kmap"]).toarray()
             Ph = np.kron(Py, Px)
             terms = [(Pz.T @ V @ Pz, Ph.T @ Hh @ Ph) for V, Hh in terms]
+
+
+def test_shift_form_center_gradient():
+    """Eq. 3 at the element centers of a shift-form grid: J = [[J2, 0],
+    [z'^T, h/2]] there, so d lambda/dz = (2/h) g_3 and (d lambda/dx,
+    d lambda/dy) = J2^-T (g_h - z' d lambda/dz) with g the reference
+    gradient, from the column's center Jacobian and the layer thickness
+    alone.  Against the oracle's recovery with its full element Jacobians."""
+    c = synth.single_hill(6, 5, 3, sigma=60.0, height=30.0, a=(1.0, 2.0, 0.5))
+    rng = np.random.default_rng(3)
+    lam = rng.normal(size=(c.nz + 1, c.ny + 1, c.nx + 1))
+    a2 = np.asarray(c.a, dtype=float) ** 2
+    u = np.zeros((3, c.nz, c.ny, c.nx))
+    for j in range(c.ny):
+        for i in range(c.nx):
+            xs, ys, zs = (A[0, j:j + 2, i:i + 2].ravel() for A in (c.X, c.Y, c.Z))  # p = a + 2b
+            J2 = 0.25 * np.array([[(xs[1] - xs[0]) + (xs[3] - xs[2]), (xs[2] - xs[0]) + (xs[3] - xs[1])],
+                                  [(ys[1] - ys[0]) + (ys[3] - ys[2]), (ys[2] - ys[0]) + (ys[3] - ys[1])]])
+            zp = 0.25 * np.array([(zs[1] - zs[0]) + (zs[3] - zs[2]), (zs[2] - zs[0]) + (zs[3] - zs[1])])
+            for k in range(c.nz):
+                h = c.Z[k + 1, 0, 0] - c.Z[k, 0, 0]
+                l = lam[k:k + 2, j:j + 2, i:i + 2]            # [c][b][a]
+                g = 0.125 * np.array([(l[:, :, 1] - l[:, :, 0]).sum(),
+                                      (l[:, 1, :] - l[:, 0, :]).sum(),
+                                      (l[1] - l[0]).sum()])
+                gz = 2.0 / h * g[2]
+                gh = np.linalg.solve(J2.T, g[:2] - zp * gz)
+                u0c = c.u0[:, k:k + 2, j:j + 2, i:i + 2].mean(axis=(1, 2, 3))
+                u[:, k, j, i] = u0c + np.array([gh[0], gh[1], gz]) / a2
+    ref = oracle.recover(c, lam.ravel())
+    assert np.abs(u - ref).max() <= 1e-12 * np.abs(ref).max()
