@@ -2,11 +2,16 @@
 """Benchmark of the mass-consistent wind solve on the 3000 x 3000 x 15 cell
 terrain-following domain (about 1.44e8 nodes, 1.35e8 free unknowns).
 
-One step = the whole hot path on one synthetic problem: stiffness assembly
-(2x2x2 Gauss) + Galerkin hierarchy + coarsest inverse, then a cold solve
-(load vector + V-cycles to a 1e-8 relative residual) + recovery of u, then
-a warm-started solve for the next time step's wind (u0 perturbed by 2 %) +
-recovery.  value = free unknowns x V-cycles / second over the timed steps.
+One step = the whole hot path on one synthetic problem: assembly (2x2x2
+Gauss; with the default separable operator the column and layer factors and
+the finest float64 rows) + Galerkin hierarchy + coarsest inverse, then a
+cold solve (load vector + float32 V-cycles inside float64 refinement, the
+residual checked every 6 cycles, to a 1e-8 relative residual) + recovery of
+u, then a warm-started solve for the next time step's wind (u0 perturbed by
+2 %) + recovery.  value = free unknowns x V-cycles / second over the timed
+steps; the line also carries the time to 1e-8 of the mixed, mixed + CG and
+plain float64 forms, the per-class rooflines, the end-to-end figure with
+host buffers, the 96-domain batch and the CPU oracle baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
